@@ -1,0 +1,183 @@
+/*
+ * curldiv.h — C ABI of the GB300 (sm_103a) solver library for the isogeometric
+ * curl-div problem
+ *
+ *     alpha (curl u, curl v) + beta (div u, div v) = (f, v)   for all v in V_h
+ *
+ * (Section 1, eq:curl-div), discretised with tensor-product B-splines of degree p
+ * on n uniform intervals per direction of the unit square (d = 2) or cube
+ * (d = 3), homogeneous Dirichlet conditions imposed strongly (Section 3.1,
+ * eq:tensor2D).  The Galerkin matrix is eq:matr_Amu (d = 2) / eq:matr_Amu3D
+ * (d = 3); the linear system solved is eq:system, A w = b.
+ *
+ * Vector layout (every entry point, host or device): FP64 (or FP32 where the name
+ * says so), C order [nrhs][d][m]...[m] with m = n + p - 2, i.e. component-major
+ * (w = [u^1; ...; u^d], Section 4, eq:eq_1) and, inside a component, the
+ * Kronecker order of the tensor index with x_1 slowest and x_d fastest.  One
+ * right-hand side has d * m^d entries (cd_dofs).
+ *
+ * Parameters: each entry point that takes `alphas` / `betas` reads nrhs host
+ * doubles (one (alpha, beta) pair per right-hand side, so one batched call can
+ * mix parameters); NULL means "the handle's alpha / beta for every RHS".  Every
+ * alpha and beta must be finite and > 0 (A is then SPD, Section 5, Thm 5.2/5.6).
+ *
+ * Ownership: the caller owns every vector it passes (device pointers unless the
+ * name ends in _host).  The library owns all of its device state (1D bands, the
+ * multigrid hierarchy, eigenbases, workspace, captured graphs); cd_destroy frees it.
+ * All device work is ordered on the stream given to cd_create.
+ *
+ * Errors: every entry point returns a cd_status and never throws or aborts
+ * across the ABI.  CD_EINVAL: bad dimension (d not 2 or 3, p < 1, n < 1,
+ * m < 2), non-finite or non-positive parameter, NULL pointer, nrhs < 1 or above
+ * the handle's batch capacity.  CD_ECUDA: a CUDA call failed (the text is
+ * available from cd_last_error).  CD_NOT_CONVERGED: maxit reached; x holds the
+ * last iterate and cd_result its residual.  CD_BREAKDOWN: a Krylov denominator
+ * was <= 0 or not finite (for example a NaN right-hand side).
+ */
+#ifndef CURLDIV_H
+#define CURLDIV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CD_API __attribute__((visibility("default")))
+
+typedef struct cd_solver_s* cd_solver;
+
+typedef enum {
+  CD_OK = 0,
+  CD_EINVAL = 1,
+  CD_ENOMEM = 2,
+  CD_ECUDA = 3,
+  CD_NOT_CONVERGED = 4,
+  CD_BREAKDOWN = 5,
+  CD_TIMEOUT = 6,
+  CD_CANCELLED = 7
+} cd_status;
+
+/* Arithmetic of the solve.
+ * CD_PREC_FP64: every kernel in FP64 (operator, Krylov vectors, preconditioner).
+ * CD_PREC_FP32_IR: FP64 iterative refinement (outer residual b - A x in FP64,
+ *   x updated in FP64) around an inner preconditioned Krylov solve whose
+ *   operator, vectors and preconditioner are FP32 (inner products in FP64). */
+enum { CD_PREC_FP64 = 0, CD_PREC_FP32_IR = 1 };
+
+/* Preconditioner of the Krylov solve.
+ * CD_PC_NONE: plain CG (the "CG" column of Tables 1-4, Section 6.2).
+ * CD_PC_FD_D: exact inverse of the block diagonal D = blockdiag(A^(c,c)) of
+ *   eq:diag by Kronecker fast diagonalisation (generalized eigenbasis of (S, M)).
+ * CD_PC_FD_T: inverse of T = I_d (x) T_m(m_{p-1}) (x) ... of eq:kron_precond,
+ *   by fast diagonalisation of the 1D factor.
+ * CD_PC_MG: one V-cycle of the Galerkin multigrid of Section 6.1 (block
+ *   prolongator eq:2by2prol, R = P^T, A_{l+1} = P^T A_l P) with a parallel
+ *   smoother; the outer Krylov method is then flexible CG. */
+enum { CD_PC_NONE = 0, CD_PC_FD_D = 1, CD_PC_FD_T = 2, CD_PC_MG = 3 };
+
+typedef struct {
+  int precision;      /* CD_PREC_*                      (default CD_PREC_FP32_IR) */
+  int precond;        /* CD_PC_*                        (default CD_PC_FD_D)      */
+  int maxit;          /* max Krylov iterations in total (default 20000)          */
+  double rtol;        /* stop when ||b - A x||_2 / ||b||_2 <= rtol (default 1e-10) */
+  int max_batch;      /* RHS capacity of one call       (default 64)             */
+  double inner_rtol;  /* FP32-IR: inner relative tolerance (default 1e-5)         */
+  int inner_maxit;    /* FP32-IR: inner iteration cap per refinement step (4000)  */
+  int max_outer;      /* FP32-IR: refinement steps before giving up (default 30)  */
+  int smoother_degree;/* MG: Chebyshev smoothing steps per visit (default 2)      */
+  int mg_m_min;       /* MG: stop coarsening at m <= mg_m_min (default 3)         */
+  int use_graphs;     /* capture the Krylov iteration in CUDA graphs (default 1)  */
+  int chunk;          /* iterations per graph launch / host convergence poll (8)  */
+  int reserved[8];
+} cd_options;
+
+typedef struct {
+  int iters_outer;    /* refinement steps (1 for CD_PREC_FP64)                  */
+  int iters_inner;    /* Krylov iterations summed over refinement steps         */
+  double relres;      /* final ||b - A x|| / ||b|| measured in FP64             */
+  double seconds;     /* wall time of the call (whole batch)                    */
+  int status;         /* cd_status of this right-hand side                      */
+} cd_result;
+
+/* Fills *opt with the defaults listed above. */
+CD_API void cd_default_options(cd_options* opt);
+
+/* d * (n + p - 2)^d, the number of unknowns of one right-hand side (Section 5.1);
+ * 0 for invalid arguments. */
+CD_API size_t cd_dofs(int d, int p, int n);
+
+CD_API const char* cd_strerror(cd_status s);
+/* Text of the last CUDA / argument error seen by this thread ("" if none). */
+CD_API const char* cd_last_error(void);
+
+/* Builds a solver for (d, p, n): 1D B-spline mass / advection / stiffness bands
+ * (eq:matr_M, eq:matr_A, eq:matr_S, Gauss-Legendre quadrature, FP64), the
+ * multigrid hierarchy, the FD eigenbases (when the preconditioner needs them) and
+ * the workspace for opt->max_batch right-hand sides.  alpha, beta are the
+ * defaults used when a call passes NULL parameter arrays.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  opt == NULL selects defaults. */
+CD_API cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha,
+                           double beta, const cd_options* opt, void* cuda_stream);
+CD_API cd_status cd_destroy(cd_solver h);
+
+/* y = A w for nrhs right-hand sides (matrix-free, sum-factorised; eq:matr_Amu /
+ * eq:matr_Amu3D).  Device pointers, FP64 / FP32 respectively. */
+CD_API cd_status cd_apply(cd_solver h, const double* w, double* y, int nrhs,
+                          const double* alphas, const double* betas);
+CD_API cd_status cd_apply_f32(cd_solver h, const float* w, float* y, int nrhs,
+                              const double* alphas, const double* betas);
+
+/* Solves A x = b (eq:system) for nrhs right-hand sides from x_0 = 0 with the
+ * handle's options; stop rule ||b - A x|| / ||b|| <= rtol (Section 6.2 with the
+ * handle's tolerance).  b, x: device FP64.  res: nrhs host entries (may be NULL).
+ * Returns the worst per-RHS status. */
+CD_API cd_status cd_solve(cd_solver h, const double* b, double* x, int nrhs,
+                          const double* alphas, const double* betas, cd_result* res);
+
+/* As cd_solve with host b and x (pageable or pinned): copies b to the device,
+ * solves, copies x back; all three steps are inside the call. */
+CD_API cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host,
+                               int nrhs, const double* alphas, const double* betas,
+                               cd_result* res);
+
+/* One application z = B^{-1} r of a preconditioner kind (CD_PC_FD_D: D^{-1},
+ * eq:diag; CD_PC_FD_T: T^{-1}, eq:kron_precond; CD_PC_MG: one V-cycle from
+ * zero) in FP64 (`f32` = 0) or FP32 (`f32` = 1, pointers then hold floats).
+ * Device pointers.  CD_EINVAL if the handle was created without the data the
+ * kind needs (FD kinds need an FD preconditioner or CD_PC_MG needs... see
+ * cd_create: every handle builds all three). */
+CD_API cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs,
+                            const double* alphas, const double* betas, int f32);
+
+/* Copies the library's 1D bands of multigrid level `level` (0 = finest) to host
+ * arrays of m_l * (2P+1) doubles each, row i holding X(i, i-P .. i+P):
+ * M, A (advection, stored exactly skew), S.  *m_out = m_l, *P_out = P.
+ * Any of M, A, S may be NULL to only query the sizes. */
+CD_API cd_status cd_get_bands(cd_solver h, int level, double* M, double* A, double* S,
+                              int* m_out, int* P_out);
+
+/* Number of multigrid levels of the handle. */
+CD_API int cd_levels(cd_solver h);
+
+/* Copies an FD eigenbasis to host: which = 0: S U = M U diag(lam), U^T M U = I
+ * (generalized, for D); which = 1: T_1 U = U diag(lam), U^T U = I (for T).
+ * U: m*m doubles, row-major U[i*m + k] = entry (i, k), columns = eigenvectors,
+ * lam ascending. */
+CD_API cd_status cd_get_eig(cd_solver h, int which, double* U, double* lam);
+
+/* Multigrid transfer between level l and l+1 (eq:2by2prol), FP64 device:
+ * cd_restrict: coarse = P^T fine; cd_prolong: fine += P coarse. */
+CD_API cd_status cd_restrict(cd_solver h, int level, const double* fine, double* coarse,
+                             int nrhs);
+CD_API cd_status cd_prolong(cd_solver h, int level, const double* coarse, double* fine,
+                            int nrhs);
+
+/* Number of this library's kernels launched by the calling thread so far. */
+CD_API uint64_t cd_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CURLDIV_H */

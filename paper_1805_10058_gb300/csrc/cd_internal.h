@@ -1,0 +1,78 @@
+// Internal declarations shared by the host setup code, the kernels and the solver.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/curldiv.h"
+
+namespace cd {
+
+// ------------------------------------------------------------------ error handling
+void set_error(const std::string& msg);
+const char* last_error();
+void count_launch(int k = 1);
+
+#define CD_CUDA_OK(expr)                                                    \
+  do {                                                                      \
+    cudaError_t e_ = (expr);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      ::cd::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));  \
+      return CD_ECUDA;                                                      \
+    }                                                                       \
+  } while (0)
+
+// ------------------------------------------------------------------ host setup
+// 1D banded matrix: rows 0..m-1, row i holds entries (i, i-P .. i+P).
+struct Band {
+  int m = 0, P = 0;
+  std::vector<double> v;  // m * (2P+1)
+  double at(int i, int j) const {
+    int k = j - i + P;
+    return (k < 0 || k > 2 * P || j < 0 || j >= m) ? 0.0 : v[(size_t)i * (2 * P + 1) + k];
+  }
+};
+
+// B-spline mass / advection / stiffness bands of degree p on n intervals,
+// restricted to the Dirichlet basis N_2..N_{n+p-1} (m = n+p-2), half-band P >= p.
+void iga_bands(int p, int n, int P, Band& M, Band& A, Band& S);
+// T_m(m_{p-1}): entries phi_{2p-1}(p - i + j), |i-j| < p.
+void toeplitz_T_band(int p, int m, int P, Band& T);
+// Galerkin coarsening of a 1D band with the 3-tap prolongator (1/2, 1, 1/2).
+Band coarsen(const Band& X);
+// Dense symmetric (generalized) eigen-decompositions, FP64, cyclic Jacobi.
+// gen = true: solve S U = M U lam with U^T M U = I (M SPD); else T U = U lam.
+bool sym_eig(int m, const std::vector<double>& Adense, std::vector<double>& U,
+             std::vector<double>& lam);
+bool gen_eig(int m, const std::vector<double>& Mdense, const std::vector<double>& Sdense,
+             std::vector<double>& U, std::vector<double>& lam);
+std::vector<double> band_to_dense(const Band& X);
+// Cholesky inverse of a small dense SPD matrix (FP64); false if not SPD.
+bool spd_inverse(int n, std::vector<double>& a);
+
+// ------------------------------------------------------------------ kernel launchers
+struct Coef {  // per-solve operator coefficients, device arrays of length >= B
+  const double* alpha;
+  const double* beta;
+};
+
+// y = A w (mode 0) or y = b - A w (mode 1) on one level; optional per-solve partial dots
+// dotp[b * nblk + blk] = sum over the block of w * y (mode 0) or y * y (mode 1).
+template <typename T>
+int launch_apply(int d, int m, int P, const T* bands /*M,A,S*/, const T* w, T* y,
+                 const T* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                 const int* active, T* scratch, cudaStream_t s);
+
+// Sets kernel attributes (dynamic shared memory caps); call once before launches/captures.
+int prepare_kernels();
+
+// generic reductions / vector kernels (per solve, deterministic)
+int partial_blocks(long long N);
+template <typename T>
+int launch_dot(const T* a, const T* b, long long N, int B, double* part, int nblk,
+               const int* active, cudaStream_t s);
+int launch_sum_partials(const double* part, int nblk, int B, double* out, cudaStream_t s);
+
+}  // namespace cd

@@ -1,0 +1,393 @@
+// CUDA kernels (sm_103a) of the curl-div solve loop.
+//
+// Layout of a batch of vectors: [B][d][m]^d, x_d fastest (component-major, Kronecker
+// order).  1D bands: [3][m][2P+1] = (M, A, S), row i holding X(i, i-P .. i+P).
+// Per-solve operator coefficients alpha[b], beta[b] (FP64); gamma = alpha - beta.
+//
+// The block operator is applied in the form (A^T = -A turns every off-diagonal
+// Kronecker term of eq:matr_Amu / eq:matr_Amu3D into gamma A(x)A(x)...):
+//   d = 2:  y1 = alpha M(x)S w1 + beta S(x)M w1 + gamma A(x)A w2
+//           y2 = gamma A(x)A w1 + alpha S(x)M w2 + beta M(x)S w2
+//   d = 3:  y1 = [alpha (MMS + MSM) + beta SMM] w1 + gamma AAM w2 + gamma AMA w3
+//           y2 = gamma AAM w1 + [alpha (SMM + MMS) + beta MSM] w2 + gamma MAA w3
+//           y3 = gamma AMA w1 + gamma MAA w2 + [alpha (SMM + MSM) + beta MMS] w3
+// (X1 X2 X3 = X1 (x) X2 (x) X3, X1 acting along x_1.)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "cd_internal.h"
+
+namespace cd {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of a double (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+__device__ double block_sum(double v) {
+  __shared__ double red[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (wid == 0) {
+    s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// ------------------------------------------------------------------ 2D fused apply
+// One CTA: TR output rows (axis x_1) of one solve, all m columns (axis x_2), both
+// components.  Shared memory: bands [3][m][W], input rows [2][TR+2P][m] (zero outside
+// the domain), intermediates [6][TR][m].
+template <typename T>
+__global__ void __launch_bounds__(256) apply2d_kernel(int m, int P, int TR,
+                                                      const T* __restrict__ bands,
+                                                      const T* __restrict__ w, T* __restrict__ y,
+                                                      const T* __restrict__ rhs, int mode,
+                                                      const double* __restrict__ alpha,
+                                                      const double* __restrict__ beta,
+                                                      const int* __restrict__ active,
+                                                      double* __restrict__ dotp) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sb = reinterpret_cast<T*>(smem_raw);
+  const int W = 2 * P + 1;
+  const int HR = TR + 2 * P;
+  T* sw = sb + 3 * m * W;
+  T* su = sw + 2 * HR * m;
+  const long long N = 2LL * m * m;
+  const long long base = (long long)b * N;
+  const int r0 = blockIdx.x * TR;
+  const int nt = blockDim.x;
+  for (int idx = threadIdx.x; idx < 3 * m * W; idx += nt) sb[idx] = bands[idx];
+  for (int idx = threadIdx.x; idx < 2 * HR * m; idx += nt) {
+    const int c = idx / (HR * m), rem = idx - c * HR * m;
+    const int rr = rem / m, j = rem - rr * m;
+    const int row = r0 - P + rr;
+    sw[idx] = (row >= 0 && row < m) ? w[base + (long long)c * m * m + (long long)row * m + j] : T(0);
+  }
+  __syncthreads();
+  const T a = T(alpha[b]), be = T(beta[b]), g = T(alpha[b] - beta[b]);
+  const T* Mb = sb;
+  const T* Ab = sb + m * W;
+  const T* Sb = sb + 2 * m * W;
+  const int rows = min(TR, m - r0);
+  // axis x_1 (slow): u = X w along rows, six intermediates premultiplied by their weights
+  for (int idx = threadIdx.x; idx < rows * m; idx += nt) {
+    const int r = idx / m, j = idx - r * m;
+    const int i = r0 + r;
+    T uM1 = 0, uS1 = 0, uA1 = 0, uM2 = 0, uS2 = 0, uA2 = 0;
+    const T* s1 = sw + (size_t)r * m + j;
+    const T* s2 = sw + (size_t)(HR + r) * m + j;
+    for (int k = 0; k < W; ++k) {
+      const T mk = Mb[i * W + k], ak = Ab[i * W + k], sk = Sb[i * W + k];
+      const T v1 = s1[(size_t)k * m], v2 = s2[(size_t)k * m];
+      uM1 += mk * v1; uS1 += sk * v1; uA1 += ak * v1;
+      uM2 += mk * v2; uS2 += sk * v2; uA2 += ak * v2;
+    }
+    const size_t o = (size_t)r * m + j, st = (size_t)TR * m;
+    su[0 * st + o] = a * uM1;   // -> S along x_2 for y1
+    su[1 * st + o] = be * uS1;  // -> M along x_2 for y1
+    su[2 * st + o] = g * uA2;   // -> A along x_2 for y1
+    su[3 * st + o] = g * uA1;   // -> A along x_2 for y2
+    su[4 * st + o] = a * uS2;   // -> M along x_2 for y2
+    su[5 * st + o] = be * uM2;  // -> S along x_2 for y2
+  }
+  __syncthreads();
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < rows * m; idx += nt) {
+    const int r = idx / m, j = idx - r * m;
+    const int i = r0 + r;
+    T y1 = 0, y2 = 0;
+    const size_t st = (size_t)TR * m;
+    const T* u = su + (size_t)r * m;
+    const int k0 = max(0, P - j), k1 = min(W - 1, m - 1 - j + P);
+    for (int k = k0; k <= k1; ++k) {
+      const int q = j + k - P;
+      const T mk = Mb[j * W + k], ak = Ab[j * W + k], sk = Sb[j * W + k];
+      y1 += sk * u[0 * st + q] + mk * u[1 * st + q] + ak * u[2 * st + q];
+      y2 += ak * u[3 * st + q] + mk * u[4 * st + q] + sk * u[5 * st + q];
+    }
+    const long long o1 = base + (long long)i * m + j, o2 = o1 + (long long)m * m;
+    if (mode == 1) {
+      y1 = rhs[o1] - y1;
+      y2 = rhs[o2] - y2;
+      acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
+    } else {
+      acc += (double)sw[(size_t)(r + P) * m + j] * (double)y1 +
+             (double)sw[(size_t)(HR + r + P) * m + j] * (double)y2;
+    }
+    y[o1] = y1;
+    y[o2] = y2;
+  }
+  if (dotp) {
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) dotp[(size_t)b * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// ------------------------------------------------------------------ generic banded axis pass
+// out_o = sum_t coef_t * (X_t along `axis`) in_{src_t}, for up to 9 outputs per launch.
+// Every array is one component [B][m]^d with its own batch stride.
+struct AxisTerm {
+  int src, band, coef;  // band: 0 = M, 1 = A, 2 = S; coef: 0 = 1, 1 = alpha, 2 = beta, 3 = gamma
+};
+template <typename T>
+struct AxisParams {
+  const T* in[9];
+  long long in_bs[9];
+  T* out[9];
+  long long out_bs[9];
+  int nt[9];
+  AxisTerm t[9][3];
+  int nout;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) axis_pass_kernel(AxisParams<T> prm, int d, int m, int P,
+                                                        int axis, const T* __restrict__ bands,
+                                                        const double* __restrict__ alpha,
+                                                        const double* __restrict__ beta,
+                                                        const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  long long npts = m;
+  for (int l = 1; l < d; ++l) npts *= m;
+  long long stride = 1;
+  for (int l = axis + 1; l < d; ++l) stride *= m;
+  const int W = 2 * P + 1;
+  const T cf[4] = {T(1), T(alpha[b]), T(beta[b]), T(alpha[b] - beta[b])};
+  for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < npts;
+       pt += (long long)gridDim.x * blockDim.x) {
+    const int ia = (int)((pt / stride) % m);
+    const int k0 = max(0, P - ia), k1 = min(W - 1, m - 1 - ia + P);
+    for (int o = 0; o < prm.nout; ++o) {
+      T acc = 0;
+      for (int t = 0; t < prm.nt[o]; ++t) {
+        const AxisTerm tm = prm.t[o][t];
+        const T* in = prm.in[tm.src] + (long long)b * prm.in_bs[tm.src] + pt;
+        const T* band = bands + (size_t)tm.band * m * W + (size_t)ia * W;
+        T s = 0;
+        for (int k = k0; k <= k1; ++k) s += band[k] * in[(long long)(k - P) * stride];
+        acc += cf[tm.coef] * s;
+      }
+      prm.out[o][(long long)b * prm.out_bs[o] + pt] = acc;
+    }
+  }
+}
+
+// y = A w (3D) via three banded passes: axis x_3 -> nine arrays T_{X,c} = X_3 w_c,
+// axis x_2 -> nine arrays P (grouped by the x_1 operator they feed), axis x_1 -> y.
+template <typename T>
+static int apply3d_multipass(int m, int P, const T* bands, const T* w, T* y, int B, Coef c,
+                             const int* active, T* scratch, cudaStream_t s) {
+  // scratch: 9 + 9 arrays of [B][m^3] followed by one [B][3 m^3] output buffer
+  const long long n3 = (long long)m * m * m;
+  const long long N = 3 * n3;
+  T* Tm = scratch;              // 9 arrays [B][m^3]: index X*3 + comp (X: 0 M, 1 A, 2 S)
+  T* Pm = scratch + 9 * n3 * B;  // 9 arrays: P1M,P1S,P1A,P2M,P2S,P2A,P3M,P3S,P3A
+  const int threads = 256;
+  long long blocks = (n3 + threads - 1) / threads;
+  dim3 grid((unsigned)std::min<long long>(blocks, 65535), B);
+  // pass 1: axis 2 (x_3)
+  AxisParams<T> a{};
+  for (int comp = 0; comp < 3; ++comp) {
+    a.in[comp] = w + comp * n3;
+    a.in_bs[comp] = N;
+  }
+  a.nout = 9;
+  for (int X = 0; X < 3; ++X)
+    for (int comp = 0; comp < 3; ++comp) {
+      const int o = X * 3 + comp;
+      a.out[o] = Tm + (long long)o * n3 * B;
+      a.out_bs[o] = n3;
+      a.nt[o] = 1;
+      a.t[o][0] = AxisTerm{comp, X, 0};
+    }
+  axis_pass_kernel<T><<<grid, threads, 0, s>>>(a, 3, m, P, 2, bands, c.alpha, c.beta, active);
+  // pass 2: axis 1 (x_2).  Inputs: T arrays (index X*3 + comp).
+  AxisParams<T> q{};
+  for (int i = 0; i < 9; ++i) {
+    q.in[i] = Tm + (long long)i * n3 * B;
+    q.in_bs[i] = n3;
+  }
+  auto TI = [](int X, int comp) { return X * 3 + comp; };  // X: 0 M, 1 A, 2 S
+  const int M_ = 0, A_ = 1, S_ = 2;
+  const int one = 0, al = 1, be = 2, ga = 3;
+  q.nout = 9;
+  for (int o = 0; o < 9; ++o) {
+    q.out[o] = Pm + (long long)o * n3 * B;
+    q.out_bs[o] = n3;
+  }
+  // P1M = alpha (M2 T_S1 + S2 T_M1); P1S = beta M2 T_M1; P1A = gamma (A2 T_M2 + M2 T_A3)
+  q.nt[0] = 2; q.t[0][0] = {TI(S_, 0), M_, al}; q.t[0][1] = {TI(M_, 0), S_, al};
+  q.nt[1] = 1; q.t[1][0] = {TI(M_, 0), M_, be};
+  q.nt[2] = 2; q.t[2][0] = {TI(M_, 1), A_, ga}; q.t[2][1] = {TI(A_, 2), M_, ga};
+  // P2M = alpha M2 T_S2 + beta S2 T_M2 + gamma A2 T_A3; P2S = alpha M2 T_M2; P2A = gamma A2 T_M1
+  q.nt[3] = 3; q.t[3][0] = {TI(S_, 1), M_, al}; q.t[3][1] = {TI(M_, 1), S_, be};
+  q.t[3][2] = {TI(A_, 2), A_, ga};
+  q.nt[4] = 1; q.t[4][0] = {TI(M_, 1), M_, al};
+  q.nt[5] = 1; q.t[5][0] = {TI(M_, 0), A_, ga};
+  // P3M = alpha S2 T_M3 + beta M2 T_S3 + gamma A2 T_A2; P3S = alpha M2 T_M3; P3A = gamma M2 T_A1
+  q.nt[6] = 3; q.t[6][0] = {TI(M_, 2), S_, al}; q.t[6][1] = {TI(S_, 2), M_, be};
+  q.t[6][2] = {TI(A_, 1), A_, ga};
+  q.nt[7] = 1; q.t[7][0] = {TI(M_, 2), M_, al};
+  q.nt[8] = 1; q.t[8][0] = {TI(A_, 0), M_, ga};
+  (void)one;
+  axis_pass_kernel<T><<<grid, threads, 0, s>>>(q, 3, m, P, 1, bands, c.alpha, c.beta, active);
+  // pass 3: axis 0 (x_1): y_c = M1 P_cM + S1 P_cS + A1 P_cA
+  AxisParams<T> r{};
+  for (int i = 0; i < 9; ++i) {
+    r.in[i] = Pm + (long long)i * n3 * B;
+    r.in_bs[i] = n3;
+  }
+  r.nout = 3;
+  for (int comp = 0; comp < 3; ++comp) {
+    r.out[comp] = y + comp * n3;
+    r.out_bs[comp] = N;
+    r.nt[comp] = 3;
+    r.t[comp][0] = {comp * 3 + 0, M_, 0};
+    r.t[comp][1] = {comp * 3 + 1, S_, 0};
+    r.t[comp][2] = {comp * 3 + 2, A_, 0};
+  }
+  axis_pass_kernel<T><<<grid, threads, 0, s>>>(r, 3, m, P, 0, bands, c.alpha, c.beta, active);
+  count_launch(3);
+  return 0;
+}
+
+// residual / dot post-pass for the multipass 3D apply
+template <typename T>
+__global__ void __launch_bounds__(256) post3d_kernel(long long N, const T* __restrict__ w,
+                                                     const T* ytmp, T* y, const T* rhs,
+                                                     int mode, const int* __restrict__ active,
+                                                     double* __restrict__ dotp) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const long long chunk = (N + gridDim.x - 1) / gridDim.x;
+  const long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  const long long base = (long long)b * N;
+  double acc = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    T v = ytmp[base + i];
+    if (mode == 1) {
+      v = rhs[base + i] - v;
+      y[base + i] = v;
+      acc += (double)v * (double)v;
+    } else {
+      acc += (double)w[base + i] * (double)v;
+    }
+  }
+  if (dotp) {
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) dotp[(size_t)b * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+int partial_blocks(long long N) {
+  long long nb = (N + 4095) / 4096;
+  return (int)std::max<long long>(1, std::min<long long>(nb, 256));
+}
+
+template <typename T>
+size_t apply2d_smem(int m, int P, int TR) {
+  return sizeof(T) * ((size_t)3 * m * (2 * P + 1) + (size_t)2 * (TR + 2 * P) * m + (size_t)6 * TR * m);
+}
+
+static constexpr size_t kApplySmemCap = 200 * 1024;
+
+int prepare_kernels() {
+  cudaError_t e1 = cudaFuncSetAttribute(apply2d_kernel<double>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmemCap);
+  cudaError_t e2 = cudaFuncSetAttribute(apply2d_kernel<float>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmemCap);
+  return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : 1;
+}
+
+template <typename T>
+int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T* rhs, int mode,
+                 int B, Coef c, double* dotp, int* nblk, const int* active, T* scratch,
+                 cudaStream_t s) {
+  if (d == 2) {
+    int TR = sizeof(T) == 8 ? 4 : 8;
+    while (TR > 1 && apply2d_smem<T>(m, P, TR) > kApplySmemCap) TR /= 2;
+    size_t sm = apply2d_smem<T>(m, P, TR);
+    dim3 grid((m + TR - 1) / TR, B);
+    apply2d_kernel<T><<<grid, 256, sm, s>>>(m, P, TR, bands, w, y, rhs, mode, c.alpha, c.beta,
+                                            active, dotp);
+    count_launch();
+    if (nblk) *nblk = grid.x;
+    return 0;
+  }
+  const long long N = 3LL * m * m * m;
+  T* ytmp = mode == 1 ? scratch + 18LL * (N / 3) * B : y;
+  apply3d_multipass<T>(m, P, bands, w, ytmp, B, c, active, scratch, s);
+  const int nb = partial_blocks(N);
+  if (dotp || mode == 1) {
+    post3d_kernel<T><<<dim3(nb, B), 256, 0, s>>>(N, w, ytmp, y, rhs, mode, active, dotp);
+    count_launch();
+  }
+  if (nblk) *nblk = nb;
+  return 0;
+}
+
+template int launch_apply<double>(int, int, int, const double*, const double*, double*,
+                                  const double*, int, int, Coef, double*, int*, const int*,
+                                  double*, cudaStream_t);
+template int launch_apply<float>(int, int, int, const float*, const float*, float*, const float*,
+                                 int, int, Coef, double*, int*, const int*, float*, cudaStream_t);
+
+// ------------------------------------------------------------------ reductions and vectors
+template <typename T, typename U>
+__global__ void __launch_bounds__(256) dot_kernel(long long N, const T* __restrict__ a,
+                                                  const U* __restrict__ bv,
+                                                  const int* __restrict__ active,
+                                                  double* __restrict__ part) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const long long chunk = (N + gridDim.x - 1) / gridDim.x;
+  const long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
+  const long long base = (long long)b * N;
+  double acc = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    acc += (double)a[base + i] * (double)bv[base + i];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = s;
+}
+
+template <typename T>
+int launch_dot(const T* a, const T* b, long long N, int B, double* part, int nblk,
+               const int* active, cudaStream_t s) {
+  dot_kernel<T, T><<<dim3(nblk, B), 256, 0, s>>>(N, a, b, active, part);
+  count_launch();
+  return 0;
+}
+template int launch_dot<double>(const double*, const double*, long long, int, double*, int,
+                                const int*, cudaStream_t);
+template int launch_dot<float>(const float*, const float*, long long, int, double*, int,
+                               const int*, cudaStream_t);
+
+__global__ void sum_partials_kernel(const double* __restrict__ part, int nblk, int B,
+                                    double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double s = 0.0;
+  for (int i = 0; i < nblk; ++i) s += part[(size_t)b * nblk + i];
+  out[b] = s;
+}
+
+int launch_sum_partials(const double* part, int nblk, int B, double* out, cudaStream_t s) {
+  sum_partials_kernel<<<(B + 127) / 128, 128, 0, s>>>(part, nblk, B, out);
+  count_launch();
+  return 0;
+}
+
+}  // namespace cd

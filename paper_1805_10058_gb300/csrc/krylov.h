@@ -1,0 +1,64 @@
+// Declarations of the Krylov / FD launch wrappers (krylov.cu) and multigrid kernels (mg.cu).
+#pragma once
+#include "cd_internal.h"
+
+namespace cd {
+
+// Per-solve scalar state of a (flexible) preconditioned CG, device arrays of length B.
+struct PcgState {
+  double* rz;
+  double* rr;
+  double* rr0;
+  double* alpha;
+  double* beta;
+  double* rzold;
+  int* active;
+  int* iters;
+  int* status;
+};
+
+// Epilogue of the last forward FD pass: divide by sum_l c_{comp,l} lam[k_l] (mode 1, FD of
+// the block diagonal D, c = beta on the component's own axis and alpha elsewhere) or by
+// prod_l lam[k_l] (mode 2, FD of T).  `base` is the start of the output tensor.
+template <typename T>
+struct FdScale {
+  int mode;
+  int d, m;
+  long long per;  // m^d
+  const T* lam;
+  const double* alpha;
+  const double* beta;
+  const T* base;
+};
+
+template <typename T>
+int launch_fd_axis(int d, int m, int axis, int B, const T* G, const T* in, T* out,
+                   FdScale<T> sc, const int* active, cudaStream_t s);
+
+template <typename T>
+void vcopy(long long N, int B, const T* src, T* dst, const int* active, cudaStream_t s);
+template <typename T>
+void vzero(long long N, int B, T* dst, const int* active, cudaStream_t s);
+template <typename T>
+void cg_update(long long N, int B, int nblk, T* x, T* r, const T* p, const T* q, const T* zold,
+               const double* alpha, const int* active, double* part_rr, double* part_rz,
+               cudaStream_t s);
+template <typename T>
+void xpay(long long N, int B, const T* z, T* p, const double* beta, const int* active,
+          cudaStream_t s);
+void ir_cast(long long N, int B, const double* r64, float* r32, const double* rnorm,
+             const int* active, cudaStream_t s);
+void ir_update(long long N, int B, double* x64, const float* e32, const double* rnorm,
+               const int* active, cudaStream_t s);
+void cg_init(int B, PcgState st, const double* prr, int nrr, const double* prz, int nrz,
+             const int* outer_active, cudaStream_t s);
+void cg_alpha(int B, PcgState st, const double* ppq, int npq, cudaStream_t s);
+void cg_check(int B, PcgState st, const double* prr, int nrr, const double* prz, int nrz,
+              double tol2, int maxit, cudaStream_t s);
+void cg_beta(int B, PcgState st, const double* prz, int nrz, int flexible, cudaStream_t s);
+void count_active(int B, const int* active, int* out, cudaStream_t s);
+void ir_check(int B, const double* prr, int nrr, const double* bnorm2, double* rnorm,
+              int* active, int* status, double* relres, int* outer_it, double tol2,
+              int max_outer, cudaStream_t s);
+
+}  // namespace cd

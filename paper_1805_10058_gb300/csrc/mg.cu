@@ -1,0 +1,553 @@
+// Multigrid kernels and the V-cycle (Section 6.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "krylov.h"
+#include "mg.h"
+
+namespace cd {
+
+static constexpr int kPowerIts = 14;
+static constexpr double kChebHi = 1.1, kChebRatio = 30.0;
+
+MgData::~MgData() {
+  for (void* p : owned) cudaFree(p);
+}
+
+// ------------------------------------------------------------------ transfer kernels
+// coarse(J) = sum over taps a in {0,1,2}^d of prod_l w_{a_l} fine(2 J_l + a_l), w = (1/2, 1, 1/2)
+template <typename T>
+__global__ void __launch_bounds__(256) restrict_kernel(int d, int mf, int mc, const T* __restrict__ fine,
+                                                       T* __restrict__ coarse,
+                                                       const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  long long nfc = 1, ncc = 1;
+  for (int l = 0; l < d; ++l) {
+    nfc *= mf;
+    ncc *= mc;
+  }
+  const long long total = (long long)d * ncc;
+  const T* fb = fine + (long long)b * d * nfc;
+  T* cb = coarse + (long long)b * total;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int comp = (int)(idx / ncc);
+    long long rem = idx - comp * ncc;
+    int J[3] = {0, 0, 0};
+    for (int l = d - 1; l >= 0; --l) {
+      J[l] = (int)(rem % mc);
+      rem /= mc;
+    }
+    T acc = 0;
+    const int ntap = d == 2 ? 9 : 27;
+    for (int t = 0; t < ntap; ++t) {
+      int tt = t;
+      long long off = 0;
+      T w = 1;
+      bool ok = true;
+      for (int l = 0; l < d; ++l) {
+        const int a = tt % 3;
+        tt /= 3;
+        const int i = 2 * J[l] + a;
+        if (i >= mf) {
+          ok = false;
+          break;
+        }
+        w *= (a == 1) ? T(1) : T(0.5);
+        off = off * mf + i;
+      }
+      if (ok) acc += w * fb[comp * nfc + off];
+    }
+    cb[idx] = acc;
+  }
+}
+
+// fine(i) += sum_J prod_l P(i_l, J_l) coarse(J); P(i, J) = 1 if i = 2J+1, 1/2 if i = 2J or 2J+2
+template <typename T>
+__global__ void __launch_bounds__(256) prolong_kernel(int d, int mf, int mc, const T* __restrict__ coarse,
+                                                      T* __restrict__ fine,
+                                                      const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  long long nfc = 1, ncc = 1;
+  for (int l = 0; l < d; ++l) {
+    nfc *= mf;
+    ncc *= mc;
+  }
+  const long long total = (long long)d * nfc;
+  const T* cb = coarse + (long long)b * d * ncc;
+  T* fb = fine + (long long)b * total;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int comp = (int)(idx / nfc);
+    long long rem = idx - comp * nfc;
+    int I[3] = {0, 0, 0};
+    for (int l = d - 1; l >= 0; --l) {
+      I[l] = (int)(rem % mf);
+      rem /= mf;
+    }
+    // per axis: up to two coarse indices with weights
+    int js[3][2];
+    T ws[3][2];
+    int nj[3];
+    for (int l = 0; l < d; ++l) {
+      const int i = I[l];
+      nj[l] = 0;
+      if (i & 1) {
+        const int j = (i - 1) / 2;
+        if (j < mc) {
+          js[l][nj[l]] = j;
+          ws[l][nj[l]++] = T(1);
+        }
+      } else {
+        const int j0 = i / 2, j1 = i / 2 - 1;
+        if (j0 < mc) {
+          js[l][nj[l]] = j0;
+          ws[l][nj[l]++] = T(0.5);
+        }
+        if (j1 >= 0 && j1 < mc) {
+          js[l][nj[l]] = j1;
+          ws[l][nj[l]++] = T(0.5);
+        }
+      }
+    }
+    T acc = 0;
+    if (d == 2) {
+      for (int a = 0; a < nj[0]; ++a)
+        for (int c = 0; c < nj[1]; ++c)
+          acc += ws[0][a] * ws[1][c] * cb[comp * ncc + (long long)js[0][a] * mc + js[1][c]];
+    } else {
+      for (int a = 0; a < nj[0]; ++a)
+        for (int c = 0; c < nj[1]; ++c)
+          for (int e = 0; e < nj[2]; ++e)
+            acc += ws[0][a] * ws[1][c] * ws[2][e] *
+                   cb[comp * ncc + ((long long)js[0][a] * mc + js[1][c]) * mc + js[2][e]];
+    }
+    fb[idx] += acc;
+  }
+}
+
+static inline dim3 grid_for(long long n, int B) {
+  long long nb = (n + 255) / 256;
+  nb = std::max<long long>(1, std::min<long long>(nb, 4096));
+  return dim3((unsigned)nb, B);
+}
+
+template <typename T>
+void mg_restrict(int d, int mf, int mc, int B, const T* fine, T* coarse, const int* active,
+                 cudaStream_t s) {
+  long long nc = d;
+  for (int l = 0; l < d; ++l) nc *= mc;
+  restrict_kernel<T><<<grid_for(nc, B), 256, 0, s>>>(d, mf, mc, fine, coarse, active);
+  count_launch();
+}
+template <typename T>
+void mg_prolong_add(int d, int mf, int mc, int B, const T* coarse, T* fine, const int* active,
+                    cudaStream_t s) {
+  long long nf = d;
+  for (int l = 0; l < d; ++l) nf *= mf;
+  prolong_kernel<T><<<grid_for(nf, B), 256, 0, s>>>(d, mf, mc, coarse, fine, active);
+  count_launch();
+}
+template void mg_restrict<double>(int, int, int, int, const double*, double*, const int*, cudaStream_t);
+template void mg_restrict<float>(int, int, int, int, const float*, float*, const int*, cudaStream_t);
+template void mg_prolong_add<double>(int, int, int, int, const double*, double*, const int*, cudaStream_t);
+template void mg_prolong_add<float>(int, int, int, int, const float*, float*, const int*, cudaStream_t);
+
+// ------------------------------------------------------------------ Jacobi / Chebyshev
+// 1 / diag of the block operator at (comp, multi-index): the diagonal of block c is
+// sum_l c_{c,l} prod_k X_k(i_k, i_k) with X_k = S on axis l and M elsewhere, c = beta on the
+// component's own axis and alpha on the others.
+template <typename T>
+__device__ __forceinline__ T dinv_at(int d, int m, int P, const T* bands, int comp,
+                                     const int* I, double al, double be) {
+  const int W = 2 * P + 1;
+  const T* Mb = bands;
+  const T* Sb = bands + 2 * (size_t)m * W;
+  double diag = 0.0;
+  for (int l = 0; l < d; ++l) {
+    double t = (l == comp) ? be : al;
+    for (int k = 0; k < d; ++k) t *= (double)((k == l) ? Sb[I[k] * W + P] : Mb[I[k] * W + P]);
+    diag += t;
+  }
+  return T(1.0 / diag);
+}
+
+__device__ __forceinline__ void decode(int d, int m, long long nper, long long idx, int& comp,
+                                       int* I) {
+  comp = (int)(idx / nper);
+  long long rem = idx - comp * nper;
+  for (int l = d - 1; l >= 0; --l) {
+    I[l] = (int)(rem % m);
+    rem /= m;
+  }
+}
+
+__device__ __forceinline__ void cheb_params(double lmax, double& theta, double& delta) {
+  const double hi = kChebHi * lmax, lo = hi / kChebRatio;
+  theta = 0.5 * (hi + lo);
+  delta = 0.5 * (hi - lo);
+}
+
+// d = D^{-1} r / theta; x = (xzero ? 0 : x) + d
+template <typename T>
+__global__ void __launch_bounds__(256) cheb_first_kernel(int d, int m, int P, const T* __restrict__ bands,
+                                                         const double* __restrict__ alpha,
+                                                         const double* __restrict__ beta,
+                                                         const double* __restrict__ lmax,
+                                                         const T* __restrict__ r, T* __restrict__ x,
+                                                         T* __restrict__ dv, int xzero,
+                                                         const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  long long nper = 1;
+  for (int l = 0; l < d; ++l) nper *= m;
+  const long long N = d * nper;
+  double th, de;
+  cheb_params(lmax[b], th, de);
+  const double al = alpha[b], be = beta[b];
+  const long long base = (long long)b * N;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int comp, I[3];
+    decode(d, m, nper, idx, comp, I);
+    const T v = dinv_at<T>(d, m, P, bands, comp, I, al, be) * r[base + idx] * T(1.0 / th);
+    dv[base + idx] = v;
+    x[base + idx] = (xzero ? T(0) : x[base + idx]) + v;
+  }
+}
+
+// step k >= 1: rho_k = 1/(2 sigma - rho_{k-1}); d = rho_k rho_{k-1} d + (2 rho_k / delta) D^{-1} r; x += d
+template <typename T>
+__global__ void __launch_bounds__(256) cheb_next_kernel(int d, int m, int P, const T* __restrict__ bands,
+                                                        const double* __restrict__ alpha,
+                                                        const double* __restrict__ beta,
+                                                        const double* __restrict__ lmax,
+                                                        const T* __restrict__ r, T* __restrict__ x,
+                                                        T* __restrict__ dv, int k,
+                                                        const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  long long nper = 1;
+  for (int l = 0; l < d; ++l) nper *= m;
+  const long long N = d * nper;
+  double th, de;
+  cheb_params(lmax[b], th, de);
+  const double sigma = th / de;
+  double rho_prev = 1.0 / sigma, rho = rho_prev;
+  for (int j = 1; j <= k; ++j) {
+    rho_prev = rho;
+    rho = 1.0 / (2.0 * sigma - rho_prev);
+  }
+  const T c1 = T(rho * rho_prev), c2 = T(2.0 * rho / de);
+  const double al = alpha[b], be = beta[b];
+  const long long base = (long long)b * N;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int comp, I[3];
+    decode(d, m, nper, idx, comp, I);
+    const T v = c1 * dv[base + idx] + c2 * dinv_at<T>(d, m, P, bands, comp, I, al, be) * r[base + idx];
+    dv[base + idx] = v;
+    x[base + idx] += v;
+  }
+}
+
+// ------------------------------------------------------------------ power iteration (FP64)
+__global__ void hash_init_kernel(long long N, double* v, int level) {
+  const int b = blockIdx.y;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ull + (unsigned long long)(level + 1) * 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 31;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 29;
+    v[(long long)b * N + i] = ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0 + 0.05;
+  }
+}
+
+__global__ void __launch_bounds__(256) jacobi_scale_kernel(int d, int m, int P, const double* __restrict__ bands,
+                                                           const double* __restrict__ alpha,
+                                                           const double* __restrict__ beta,
+                                                           const double* __restrict__ y,
+                                                           double* __restrict__ v) {
+  const int b = blockIdx.y;
+  long long nper = 1;
+  for (int l = 0; l < d; ++l) nper *= m;
+  const long long N = d * nper;
+  const long long base = (long long)b * N;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int comp, I[3];
+    decode(d, m, nper, idx, comp, I);
+    v[base + idx] = dinv_at<double>(d, m, P, bands, comp, I, alpha[b], beta[b]) * y[base + idx];
+  }
+}
+
+__global__ void norm_step_kernel(int B, const double* part, int nblk, double* lam_out,
+                                 double* inv_norm) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double s = 0.0;
+  for (int i = 0; i < nblk; ++i) s += part[(size_t)b * nblk + i];
+  const double nrm = sqrt(s);
+  if (lam_out) lam_out[b] = nrm;
+  inv_norm[b] = nrm > 0 ? 1.0 / nrm : 0.0;
+}
+
+__global__ void scale_kernel(long long N, double* v, const double* sc) {
+  const int b = blockIdx.y;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    v[(long long)b * N + i] *= sc[b];
+}
+
+// ------------------------------------------------------------------ coarsest solve
+template <typename T>
+__global__ void coarse_solve_kernel(int nc, const T* __restrict__ inv, const T* __restrict__ rhs,
+                                    T* __restrict__ x, const int* __restrict__ active) {
+  const int b = blockIdx.x;
+  if (active && !active[b]) return;
+  const T* Ab = inv + (size_t)b * nc * nc;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    T s = 0;
+    for (int j = 0; j < nc; ++j) s += Ab[(size_t)i * nc + j] * rhs[(size_t)b * nc + j];
+    x[(size_t)b * nc + i] = s;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+std::vector<double> dense_operator(int d, const Band& M, const Band& A, const Band& S,
+                                   double alpha, double beta) {
+  const int m = M.m;
+  long long nper = 1;
+  for (int l = 0; l < d; ++l) nper *= m;
+  const long long n = d * nper;
+  std::vector<double> D((size_t)(n * n), 0.0);
+  const double gamma = alpha - beta;
+  std::vector<int> I(d), J(d);
+  for (long long r = 0; r < n; ++r) {
+    const int c = (int)(r / nper);
+    long long rem = r % nper;
+    for (int l = d - 1; l >= 0; --l) {
+      I[l] = (int)(rem % m);
+      rem /= m;
+    }
+    for (long long q = 0; q < n; ++q) {
+      const int c2 = (int)(q / nper);
+      long long rem2 = q % nper;
+      for (int l = d - 1; l >= 0; --l) {
+        J[l] = (int)(rem2 % m);
+        rem2 /= m;
+      }
+      double v = 0.0;
+      if (c == c2) {
+        for (int l = 0; l < d; ++l) {
+          double t = (l == c) ? beta : alpha;
+          for (int k = 0; k < d; ++k) t *= (k == l) ? S.at(I[k], J[k]) : M.at(I[k], J[k]);
+          v += t;
+        }
+      } else {
+        double t = gamma;
+        for (int k = 0; k < d; ++k) t *= (k == c || k == c2) ? A.at(I[k], J[k]) : M.at(I[k], J[k]);
+        v = t;
+      }
+      D[(size_t)(r * n + q)] = v;
+    }
+  }
+  return D;
+}
+
+cd_status mg_build(MgData& mg, int d, int P, const std::vector<int>& ml,
+                   const std::vector<Band>& hM, const std::vector<Band>& hA,
+                   const std::vector<Band>& hS, int B, int deg, const double* bands64,
+                   const float* bands32, const std::vector<size_t>& boff) {
+  mg.d = d;
+  mg.P = P;
+  mg.L = (int)ml.size();
+  mg.B = B;
+  mg.deg = deg;
+  mg.ml = ml;
+  mg.boff = boff;
+  mg.bands64 = bands64;
+  mg.bands32 = bands32;
+  mg.hM = hM;
+  mg.hA = hA;
+  mg.hS = hS;
+  mg.Nl.clear();
+  for (int m : ml) {
+    long long n = d;
+    for (int l = 0; l < d; ++l) n *= m;
+    mg.Nl.push_back(n);
+  }
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    mg.owned.push_back(p);
+    return p;
+  };
+  mg.lv64.assign(mg.L, MgLevelBuf{});
+  mg.lv32.assign(mg.L, MgLevelBuf{});
+  for (int l = 0; l < mg.L; ++l) {
+    const size_t n = (size_t)mg.Nl[l] * B;
+    for (int prec = 0; prec < 2; ++prec) {
+      const size_t es = prec == 0 ? 8 : 4;
+      MgLevelBuf& lb = prec == 0 ? mg.lv64[l] : mg.lv32[l];
+      lb.b = alloc(n * es);
+      lb.x = alloc(n * es);
+      lb.r = alloc(n * es);
+      lb.dv = alloc(n * es);
+      if (!lb.b || !lb.x || !lb.r || !lb.dv) return CD_ENOMEM;
+    }
+  }
+  mg.nc = (int)mg.Nl.back();
+  mg.lmax = (double*)alloc(sizeof(double) * mg.L * B);
+  mg.cinv64 = (double*)alloc(sizeof(double) * (size_t)B * mg.nc * mg.nc);
+  mg.cinv32 = (float*)alloc(sizeof(float) * (size_t)B * mg.nc * mg.nc);
+  mg.part = (double*)alloc(sizeof(double) * (size_t)B * 1024);
+  mg.tmpB = (double*)alloc(sizeof(double) * B);
+  // 3D scratch for levels >= 1 (the finest level uses the handle's scratch)
+  if (d == 3 && mg.L > 1) {
+    const size_t n3 = (size_t)(mg.Nl[1] / 3) * B;
+    mg.scratch64 = alloc(21 * n3 * 8);
+    mg.scratch32 = alloc(21 * n3 * 4);
+    if (!mg.scratch64 || !mg.scratch32) return CD_ENOMEM;
+  }
+  if (!mg.lmax || !mg.cinv64 || !mg.cinv32 || !mg.part || !mg.tmpB) return CD_ENOMEM;
+  return CD_OK;
+}
+
+void mg_set_scratch(MgData&, void*, void*) {}
+
+template <typename T>
+static const T* level_bands(const MgData& mg, int l) {
+  if (sizeof(T) == 8) return reinterpret_cast<const T*>(mg.bands64 + mg.boff[l]);
+  return reinterpret_cast<const T*>(mg.bands32 + mg.boff[l]);
+}
+
+template <typename T>
+static T* level_scratch(MgData& mg, int l, T* fine_scratch) {
+  (void)fine_scratch;
+  return (T*)(sizeof(T) == 8 ? mg.scratch64 : mg.scratch32);
+}
+
+cd_status mg_set_params(MgData& mg, int d, int P, int nrhs, const std::vector<double>& alpha,
+                        const std::vector<double>& beta, cudaStream_t s) {
+  // coarsest dense inverses (host, FP64)
+  const int L = mg.L, nc = mg.nc;
+  std::vector<double> inv64((size_t)nrhs * nc * nc);
+  std::vector<float> inv32(inv64.size());
+  for (int b = 0; b < nrhs; ++b) {
+    std::vector<double> D = dense_operator(d, mg.hM[L - 1], mg.hA[L - 1], mg.hS[L - 1], alpha[b], beta[b]);
+    if (!spd_inverse(nc, D)) {
+      set_error("coarsest multigrid matrix is not SPD");
+      return CD_BREAKDOWN;
+    }
+    std::copy(D.begin(), D.end(), inv64.begin() + (size_t)b * nc * nc);
+  }
+  for (size_t i = 0; i < inv64.size(); ++i) inv32[i] = (float)inv64[i];
+  CD_CUDA_OK(cudaMemcpyAsync(mg.cinv64, inv64.data(), inv64.size() * 8, cudaMemcpyHostToDevice, s));
+  CD_CUDA_OK(cudaMemcpyAsync(mg.cinv32, inv32.data(), inv32.size() * 4, cudaMemcpyHostToDevice, s));
+  CD_CUDA_OK(cudaStreamSynchronize(s));  // host vectors go out of scope
+  return CD_OK;
+}
+
+// Power iteration for lambda_max(D^{-1} A_l) on every smoothed level (FP64), per solve.
+static void mg_power(MgData& mg, int B, Coef c, double* fine_scratch64, cudaStream_t s) {
+  for (int l = 0; l + 1 < mg.L; ++l) {
+    const int m = mg.ml[l];
+    const long long N = mg.Nl[l];
+    double* v = (double*)mg.lv64[l].x;
+    double* y = (double*)mg.lv64[l].r;
+    const dim3 g = grid_for(N, B);
+    hash_init_kernel<<<g, 256, 0, s>>>(N, v, l);
+    const int nb = partial_blocks(N);
+    launch_dot<double>(v, v, N, B, mg.part, nb, nullptr, s);
+    norm_step_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, mg.part, nb, nullptr, mg.tmpB);
+    scale_kernel<<<g, 256, 0, s>>>(N, v, mg.tmpB);
+    count_launch(3);
+    double* scr = l == 0 ? fine_scratch64 : (double*)mg.scratch64;
+    for (int it = 0; it < kPowerIts; ++it) {
+      launch_apply<double>(mg.d, m, mg.P, level_bands<double>(mg, l), v, y, nullptr, 0, B, c,
+                           nullptr, nullptr, nullptr, scr, s);
+      jacobi_scale_kernel<<<g, 256, 0, s>>>(mg.d, m, mg.P, level_bands<double>(mg, l), c.alpha,
+                                            c.beta, y, v);
+      launch_dot<double>(v, v, N, B, mg.part, nb, nullptr, s);
+      norm_step_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, mg.part, nb, mg.lmax + (size_t)l * mg.B,
+                                                       mg.tmpB);
+      scale_kernel<<<g, 256, 0, s>>>(N, v, mg.tmpB);
+      count_launch(3);
+    }
+  }
+}
+
+cd_status mg_prepare(MgData& mg, int B, Coef c, double* fine_scratch64, cudaStream_t s) {
+  mg_power(mg, B, c, fine_scratch64, s);
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+template <typename T>
+static void smooth(MgData& mg, int l, int B, const T* bl, T* xl, bool xzero, Coef c,
+                   const int* active, T* scr, cudaStream_t s) {
+  const int m = mg.ml[l];
+  const long long N = mg.Nl[l];
+  MgLevelBuf& lb = sizeof(T) == 8 ? mg.lv64[l] : mg.lv32[l];
+  T* r = (T*)lb.r;
+  T* dv = (T*)lb.dv;
+  const T* bands = level_bands<T>(mg, l);
+  const double* lm = mg.lmax + (size_t)l * mg.B;
+  const dim3 g = grid_for(N, B);
+  const T* rsrc = bl;
+  if (!xzero) {
+    launch_apply<T>(mg.d, m, mg.P, bands, xl, r, bl, 1, B, c, nullptr, nullptr, active, scr, s);
+    rsrc = r;
+  }
+  cheb_first_kernel<T><<<g, 256, 0, s>>>(mg.d, m, mg.P, bands, c.alpha, c.beta, lm, rsrc, xl, dv,
+                                         xzero ? 1 : 0, active);
+  count_launch();
+  for (int k = 1; k < mg.deg; ++k) {
+    launch_apply<T>(mg.d, m, mg.P, bands, dv, r, rsrc, 1, B, c, nullptr, nullptr, active, scr, s);
+    rsrc = r;
+    cheb_next_kernel<T><<<g, 256, 0, s>>>(mg.d, m, mg.P, bands, c.alpha, c.beta, lm, r, xl, dv, k,
+                                          active);
+    count_launch();
+  }
+}
+
+template <typename T>
+static void vcycle_rec(MgData& mg, int l, int B, const T* bl, T* xl, Coef c, const int* active,
+                       T* fine_scr, cudaStream_t s) {
+  T* scr = l == 0 ? fine_scr : level_scratch<T>(mg, l, fine_scr);
+  if (l == mg.L - 1) {
+    coarse_solve_kernel<T><<<B, 128, 0, s>>>(mg.nc, sizeof(T) == 8 ? (const T*)mg.cinv64 : (const T*)mg.cinv32,
+                                             bl, xl, active);
+    count_launch();
+    return;
+  }
+  MgLevelBuf& lb = sizeof(T) == 8 ? mg.lv64[l] : mg.lv32[l];
+  MgLevelBuf& nb = sizeof(T) == 8 ? mg.lv64[l + 1] : mg.lv32[l + 1];
+  smooth<T>(mg, l, B, bl, xl, true, c, active, scr, s);
+  launch_apply<T>(mg.d, mg.ml[l], mg.P, level_bands<T>(mg, l), xl, (T*)lb.r, bl, 1, B, c, nullptr,
+                  nullptr, active, scr, s);
+  mg_restrict<T>(mg.d, mg.ml[l], mg.ml[l + 1], B, (const T*)lb.r, (T*)nb.b, active, s);
+  vcycle_rec<T>(mg, l + 1, B, (const T*)nb.b, (T*)nb.x, c, active, fine_scr, s);
+  mg_prolong_add<T>(mg.d, mg.ml[l], mg.ml[l + 1], B, (const T*)nb.x, xl, active, s);
+  smooth<T>(mg, l, B, bl, xl, false, c, active, scr, s);
+}
+
+template <typename T>
+void mg_vcycle(MgData& mg, int d, int P, int B, const T* r, T* z, Coef c, const int* active,
+               cudaStream_t s, T* fine_scr) {
+  (void)d;
+  (void)P;
+  vcycle_rec<T>(mg, 0, B, r, z, c, active, fine_scr, s);
+}
+template void mg_vcycle<double>(MgData&, int, int, int, const double*, double*, Coef, const int*,
+                                cudaStream_t, double*);
+template void mg_vcycle<float>(MgData&, int, int, int, const float*, float*, Coef, const int*,
+                               cudaStream_t, float*);
+
+}  // namespace cd

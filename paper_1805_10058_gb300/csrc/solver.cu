@@ -1,0 +1,703 @@
+// Solver handle, Krylov orchestration (FP64 PCG, FP32-inner / FP64 iterative refinement),
+// preconditioners and the C-ABI entry points of include/curldiv.h.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+
+#include "krylov.h"
+#include "mg.h"
+
+namespace cd {
+uint64_t launches();
+
+// ------------------------------------------------------------------ device buffers
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t b) {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = b;
+    return b ? cudaMalloc(&p, b) : cudaSuccess;
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+template <typename T>
+static cudaError_t upload(DevBuf& d, const std::vector<T>& h) {
+  cudaError_t e = d.alloc(h.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+template <typename T>
+static std::vector<T> cast_vec(const std::vector<double>& v) {
+  std::vector<T> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+  return o;
+}
+
+struct Workspace {  // one precision's Krylov vectors
+  DevBuf x, r, z, p, q, zold, fa, fb, mg;
+  DevBuf apply_scratch;
+};
+
+}  // namespace cd
+
+using namespace cd;
+
+struct cd_solver_s {
+  int d = 0, p = 0, n = 0, m = 0, P = 0;
+  double alpha0 = 1, beta0 = 1;
+  cd_options opt{};
+  cudaStream_t s = nullptr;
+  long long N = 0;  // DoF per RHS
+  int Bcap = 0;
+  std::vector<Band> hM, hA, hS;  // per level
+  std::vector<int> ml;           // per-level m
+  DevBuf bands64, bands32;       // all levels concatenated: level l at offset boff[l]
+  std::vector<size_t> boff;
+  // FD eigenbases (finest level)
+  std::vector<double> UD, lamD, UT, lamT;
+  DevBuf UD64, UDt64, lamD64, UT64, UTt64, lamT64, UD32, UDt32, lamD32, UT32, UTt32, lamT32;
+  bool have_fd = false;
+  // per-solve coefficients and state
+  DevBuf alpha, beta;
+  DevBuf sd[6];  // rz rr rr0 alpha beta rzold
+  DevBuf si[3];  // active iters status
+  DevBuf part[4];
+  DevBuf ir_rnorm, ir_bnorm2, ir_relres, ir_active, ir_status, ir_outer, ir_inner_total, cnt;
+  DevBuf b64, x64, r64;
+  Workspace w64, w32;
+  int* h_cnt = nullptr;  // pinned
+  MgData mg;
+  // CUDA graphs of a chunk of PCG iterations, keyed by (f32, B, pc, flexible, tol, maxit)
+  std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, uint64_t>> graphs;
+  std::mutex mu;
+  ~cd_solver_s() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
+    if (h_cnt) cudaFreeHost(h_cnt);
+  }
+};
+
+namespace cd {
+
+static PcgState state_of(cd_solver h) {
+  PcgState st;
+  st.rz = h->sd[0].as<double>();
+  st.rr = h->sd[1].as<double>();
+  st.rr0 = h->sd[2].as<double>();
+  st.alpha = h->sd[3].as<double>();
+  st.beta = h->sd[4].as<double>();
+  st.rzold = h->sd[5].as<double>();
+  st.active = h->si[0].as<int>();
+  st.iters = h->si[1].as<int>();
+  st.status = h->si[2].as<int>();
+  return st;
+}
+
+template <typename T>
+static const T* bands_of(cd_solver h, int level) {
+  if (sizeof(T) == 8) return reinterpret_cast<const T*>(h->bands64.as<double>() + h->boff[level]);
+  return reinterpret_cast<const T*>(h->bands32.as<float>() + h->boff[level]);
+}
+template <typename T>
+static Workspace& ws_of(cd_solver h) {
+  return sizeof(T) == 8 ? h->w64 : h->w32;
+}
+
+static Coef coef_of(cd_solver h) { return Coef{h->alpha.as<double>(), h->beta.as<double>()}; }
+
+template <typename T>
+static void apply_level(cd_solver h, int level, const T* w, T* y, const T* rhs, int mode, int B,
+                        double* dotp, int* nblk, const int* active) {
+  launch_apply<T>(h->d, h->ml[level], h->P, bands_of<T>(h, level), w, y, rhs, mode, B,
+                  coef_of(h), dotp, nblk, active, ws_of<T>(h).apply_scratch.template as<T>(), h->s);
+}
+
+// z = B^{-1} r for the preconditioner kind pc.
+template <typename T>
+static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* active) {
+  Workspace& w = ws_of<T>(h);
+  if (pc == CD_PC_NONE) {
+    vcopy<T>(h->N, B, r, z, active, h->s);
+    return;
+  }
+  if (pc == CD_PC_MG) {
+    mg_vcycle<T>(h->mg, h->d, h->P, B, r, z, coef_of(h), active, h->s, w.apply_scratch.as<T>());
+    return;
+  }
+  const bool isD = pc == CD_PC_FD_D;
+  const T *U, *Ut, *lam;
+  if (sizeof(T) == 8) {
+    U = (const T*)(isD ? h->UD64.p : h->UT64.p);
+    Ut = (const T*)(isD ? h->UDt64.p : h->UTt64.p);
+    lam = (const T*)(isD ? h->lamD64.p : h->lamT64.p);
+  } else {
+    U = (const T*)(isD ? h->UD32.p : h->UT32.p);
+    Ut = (const T*)(isD ? h->UDt32.p : h->UTt32.p);
+    lam = (const T*)(isD ? h->lamD32.p : h->lamT32.p);
+  }
+  const int d = h->d, m = h->m;
+  T* bufs[2] = {w.fa.as<T>(), w.fb.as<T>()};
+  const T* src = r;
+  int pass = 0;
+  for (int a = d - 1; a >= 0; --a) {  // forward: U^T along every axis, then scale
+    T* dst = bufs[pass & 1];
+    FdScale<T> sc{};
+    if (a == 0) {
+      sc.mode = isD ? 1 : 2;
+      sc.d = d;
+      sc.m = m;
+      sc.per = h->N / d;
+      sc.lam = lam;
+      sc.alpha = h->alpha.as<double>();
+      sc.beta = h->beta.as<double>();
+      sc.base = dst;
+    }
+    launch_fd_axis<T>(d, m, a, B, U, src, dst, sc, active, h->s);
+    src = dst;
+    ++pass;
+  }
+  for (int a = d - 1; a >= 0; --a) {  // backward: U along every axis
+    T* dst = (a == 0) ? z : bufs[pass & 1];
+    launch_fd_axis<T>(d, m, a, B, Ut, src, dst, FdScale<T>{}, active, h->s);
+    src = dst;
+    ++pass;
+  }
+}
+
+// One PCG iteration (all kernels masked by the per-solve active flags).
+template <typename T>
+static void pcg_iteration(cd_solver h, int B, int pc, int flexible, double tol2, int maxit) {
+  Workspace& w = ws_of<T>(h);
+  PcgState st = state_of(h);
+  const long long N = h->N;
+  const int nb = partial_blocks(N);
+  int npq = 0;
+  apply_level<T>(h, 0, w.p.as<T>(), w.q.as<T>(), nullptr, 0, B, h->part[0].as<double>(), &npq,
+                 st.active);
+  cg_alpha(B, st, h->part[0].as<double>(), npq, h->s);
+  cg_update<T>(N, B, nb, w.x.as<T>(), w.r.as<T>(), w.p.as<T>(), w.q.as<T>(),
+               flexible ? w.z.as<T>() : nullptr, st.alpha, st.active, h->part[1].as<double>(),
+               h->part[2].as<double>(), h->s);
+  cg_check(B, st, h->part[1].as<double>(), nb, flexible ? h->part[2].as<double>() : nullptr, nb,
+           tol2, maxit, h->s);
+  apply_prec<T>(h, pc, B, w.r.as<T>(), w.z.as<T>(), st.active);
+  launch_dot<T>(w.r.as<T>(), w.z.as<T>(), N, B, h->part[3].as<double>(), nb, st.active, h->s);
+  cg_beta(B, st, h->part[3].as<double>(), nb, flexible, h->s);
+  xpay<T>(N, B, w.z.as<T>(), w.p.as<T>(), st.beta, st.active, h->s);
+}
+
+// Runs PCG on the workspace of precision T: r holds the right-hand side on entry, x the
+// solution on exit (x_0 = 0).  outer_active masks the solves that take part.
+template <typename T>
+static cd_status run_pcg(cd_solver h, int B, int pc, double tol, int maxit,
+                         const int* outer_active) {
+  Workspace& w = ws_of<T>(h);
+  PcgState st = state_of(h);
+  const long long N = h->N;
+  const int nb = partial_blocks(N);
+  const int flexible = (pc == CD_PC_MG) ? 1 : 0;
+  vzero<T>(N, B, w.x.as<T>(), outer_active, h->s);
+  apply_prec<T>(h, pc, B, w.r.as<T>(), w.z.as<T>(), outer_active);
+  launch_dot<T>(w.r.as<T>(), w.r.as<T>(), N, B, h->part[1].as<double>(), nb, outer_active, h->s);
+  launch_dot<T>(w.r.as<T>(), w.z.as<T>(), N, B, h->part[3].as<double>(), nb, outer_active, h->s);
+  cg_init(B, st, h->part[1].as<double>(), nb, h->part[3].as<double>(), nb, outer_active, h->s);
+  vcopy<T>(N, B, w.z.as<T>(), w.p.as<T>(), st.active, h->s);
+  const double tol2 = tol * tol;
+  const int chunk = std::max(1, h->opt.chunk);
+  cudaGraphExec_t exec = nullptr;
+  uint64_t nodes = 0;
+  if (h->opt.use_graphs) {
+    auto key = std::make_tuple((int)(sizeof(T) == 4), B, pc, flexible, tol, maxit);
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+      exec = it->second.first;
+      nodes = it->second.second;
+    } else {
+      cudaGraph_t g = nullptr;
+      const uint64_t c0 = launches();
+      if (cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2, maxit);
+        count_active(B, st.active, h->cnt.as<int>(), h->s);
+        if (cudaStreamEndCapture(h->s, &g) == cudaSuccess && g) {
+          if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+          cudaGraphDestroy(g);
+        }
+      }
+      nodes = launches() - c0;
+      count_launch(-(int)nodes);  // captured, not launched
+      cudaGetLastError();
+      if (exec) h->graphs[key] = std::make_pair(exec, nodes);
+    }
+  }
+  for (int done = 0; done < maxit + chunk; done += chunk) {
+    if (exec) {
+      CD_CUDA_OK(cudaGraphLaunch(exec, h->s));
+      count_launch((int)nodes);
+    } else {
+      for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2, maxit);
+      count_active(B, st.active, h->cnt.as<int>(), h->s);
+    }
+    CD_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->cnt.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaStreamSynchronize(h->s));
+    if (*h->h_cnt == 0) break;
+  }
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+__global__ void add_iters_kernel(int B, const int* iters, const int* active, int* total) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B && active[b]) total[b] += iters[b];
+}
+__global__ void set_int_kernel(int B, int* a, int v) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) a[b] = v;
+}
+__global__ void d2f_kernel(long long n, const double* a, float* b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f2d_kernel(long long n, const float* a, double* b) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// Final FP64 residual ||b - A x|| / ||b|| for reporting (FP64 apply, mode 1).
+static cd_status final_residual(cd_solver h, int B, const double* b, const double* x,
+                                std::vector<double>& relres) {
+  const int nb = partial_blocks(h->N);
+  int npart = 0;
+  apply_level<double>(h, 0, x, h->r64.as<double>(), b, 1, B, h->part[0].as<double>(), &npart,
+                      nullptr);
+  launch_dot<double>(b, b, h->N, B, h->part[1].as<double>(), nb, nullptr, h->s);
+  std::vector<double> prr((size_t)B * npart), pbb((size_t)B * nb);
+  CD_CUDA_OK(cudaMemcpyAsync(prr.data(), h->part[0].p, prr.size() * 8, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(pbb.data(), h->part[1].p, pbb.size() * 8, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaStreamSynchronize(h->s));
+  relres.assign(B, 0.0);
+  for (int i = 0; i < B; ++i) {
+    double rr = 0, bb = 0;
+    for (int k = 0; k < npart; ++k) rr += prr[(size_t)i * npart + k];
+    for (int k = 0; k < nb; ++k) bb += pbb[(size_t)i * nb + k];
+    relres[i] = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  }
+  return CD_OK;
+}
+
+static cd_status set_params(cd_solver h, int nrhs, const double* alphas, const double* betas) {
+  std::vector<double> a(nrhs), b(nrhs);
+  for (int i = 0; i < nrhs; ++i) {
+    a[i] = alphas ? alphas[i] : h->alpha0;
+    b[i] = betas ? betas[i] : h->beta0;
+    if (!(a[i] > 0) || !(b[i] > 0) || !std::isfinite(a[i]) || !std::isfinite(b[i])) {
+      set_error("alpha and beta must be finite and > 0");
+      return CD_EINVAL;
+    }
+  }
+  CD_CUDA_OK(cudaMemcpyAsync(h->alpha.p, a.data(), nrhs * 8, cudaMemcpyHostToDevice, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(h->beta.p, b.data(), nrhs * 8, cudaMemcpyHostToDevice, h->s));
+  if (h->opt.precond == CD_PC_MG) {
+    cd_status st = mg_set_params(h->mg, h->d, h->P, nrhs, a, b, h->s);
+    if (st != CD_OK) return st;
+    return mg_prepare(h->mg, nrhs, coef_of(h), h->w64.apply_scratch.as<double>(), h->s);
+  }
+  return CD_OK;
+}
+
+static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd_result* res) {
+  auto t0 = std::chrono::steady_clock::now();
+  const long long N = h->N;
+  const int pc = h->opt.precond;
+  std::vector<int> status(B, CD_OK), inner(B, 0), outer(B, 1);
+  if (h->opt.precision == CD_PREC_FP64) {
+    vcopy<double>(N, B, b, h->w64.r.as<double>(), nullptr, h->s);
+    cd_status st = run_pcg<double>(h, B, pc, h->opt.rtol, h->opt.maxit, nullptr);
+    if (st != CD_OK) return st;
+    vcopy<double>(N, B, h->w64.x.as<double>(), x, nullptr, h->s);
+    CD_CUDA_OK(cudaMemcpyAsync(status.data(), h->si[2].p, B * 4, cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaMemcpyAsync(inner.data(), h->si[1].p, B * 4, cudaMemcpyDeviceToHost, h->s));
+  } else {
+    // FP64 iterative refinement around FP32 inner PCG
+    const int nb = partial_blocks(N);
+    int* act = h->ir_active.as<int>();
+    set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, act, 1);
+    set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_status.as<int>(), CD_NOT_CONVERGED);
+    set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_outer.as<int>(), 0);
+    set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_inner_total.as<int>(), 0);
+    count_launch(4);
+    vzero<double>(N, B, x, nullptr, h->s);
+    launch_dot<double>(b, b, N, B, h->part[1].as<double>(), nb, nullptr, h->s);
+    launch_sum_partials(h->part[1].as<double>(), nb, B, h->ir_bnorm2.as<double>(), h->s);
+    for (int step = 0; step <= h->opt.max_outer + 1; ++step) {
+      int npart = 0;
+      apply_level<double>(h, 0, x, h->r64.as<double>(), b, 1, B, h->part[0].as<double>(), &npart,
+                          act);
+      ir_check(B, h->part[0].as<double>(), npart, h->ir_bnorm2.as<double>(),
+               h->ir_rnorm.as<double>(), act, h->ir_status.as<int>(), h->ir_relres.as<double>(),
+               h->ir_outer.as<int>(), h->opt.rtol * h->opt.rtol, h->opt.max_outer, h->s);
+      count_active(B, act, h->cnt.as<int>(), h->s);
+      CD_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->cnt.p, 4, cudaMemcpyDeviceToHost, h->s));
+      CD_CUDA_OK(cudaStreamSynchronize(h->s));
+      if (*h->h_cnt == 0) break;
+      ir_cast(N, B, h->r64.as<double>(), h->w32.r.as<float>(), h->ir_rnorm.as<double>(), act, h->s);
+      cd_status st = run_pcg<float>(h, B, pc, h->opt.inner_rtol, h->opt.inner_maxit, act);
+      if (st != CD_OK) return st;
+      add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), act,
+                                                          h->ir_inner_total.as<int>());
+      count_launch();
+      ir_update(N, B, x, h->w32.x.as<float>(), h->ir_rnorm.as<double>(), act, h->s);
+    }
+    CD_CUDA_OK(cudaMemcpyAsync(status.data(), h->ir_status.p, B * 4, cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaMemcpyAsync(inner.data(), h->ir_inner_total.p, B * 4, cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaMemcpyAsync(outer.data(), h->ir_outer.p, B * 4, cudaMemcpyDeviceToHost, h->s));
+  }
+  std::vector<double> rel;
+  cd_status st = final_residual(h, B, b, x, rel);
+  if (st != CD_OK) return st;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  cd_status worst = CD_OK;
+  for (int i = 0; i < B; ++i) {
+    int s_i = status[i];
+    if (s_i == CD_OK && !(rel[i] <= h->opt.rtol * 10)) s_i = CD_NOT_CONVERGED;
+    if (s_i != CD_OK && worst == CD_OK) worst = (cd_status)s_i;
+    if (res) {
+      res[i].iters_outer = outer[i];
+      res[i].iters_inner = inner[i];
+      res[i].relres = rel[i];
+      res[i].seconds = secs;
+      res[i].status = s_i;
+    }
+  }
+  return worst;
+}
+
+}  // namespace cd
+
+// ====================================================================== C ABI
+extern "C" {
+
+void cd_default_options(cd_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = CD_PREC_FP32_IR;
+  o->precond = CD_PC_FD_D;
+  o->maxit = 20000;
+  o->rtol = 1e-10;
+  o->max_batch = 64;
+  o->inner_rtol = 1e-5;
+  o->inner_maxit = 4000;
+  o->max_outer = 30;
+  o->smoother_degree = 2;
+  o->mg_m_min = 3;
+  o->use_graphs = 1;
+  o->chunk = 8;
+}
+
+size_t cd_dofs(int d, int p, int n) {
+  if ((d != 2 && d != 3) || p < 1 || n < 1) return 0;
+  size_t m = (size_t)(n + p - 2), r = (size_t)d;
+  for (int l = 0; l < d; ++l) r *= m;
+  return r;
+}
+
+const char* cd_strerror(cd_status s) {
+  switch (s) {
+    case CD_OK: return "ok";
+    case CD_EINVAL: return "invalid argument";
+    case CD_ENOMEM: return "out of device memory";
+    case CD_ECUDA: return "CUDA error";
+    case CD_NOT_CONVERGED: return "not converged";
+    case CD_BREAKDOWN: return "Krylov breakdown";
+    case CD_TIMEOUT: return "timeout";
+    case CD_CANCELLED: return "cancelled";
+  }
+  return "unknown status";
+}
+
+const char* cd_last_error(void) { return cd::last_error(); }
+uint64_t cd_kernel_launches(void) { return cd::launches(); }
+
+cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double beta,
+                    const cd_options* opt, void* stream) {
+  if (!out) return CD_EINVAL;
+  *out = nullptr;
+  if ((d != 2 && d != 3) || p < 1 || n < 1 || n + p - 2 < 2) {
+    set_error("need d in {2,3}, p >= 1, n >= 1, m = n+p-2 >= 2");
+    return CD_EINVAL;
+  }
+  if (!(alpha > 0) || !(beta > 0) || !std::isfinite(alpha) || !std::isfinite(beta)) {
+    set_error("alpha and beta must be finite and > 0");
+    return CD_EINVAL;
+  }
+  std::unique_ptr<cd_solver_s> h(new cd_solver_s());
+  h->d = d;
+  h->p = p;
+  h->n = n;
+  h->m = n + p - 2;
+  h->P = p;
+  h->alpha0 = alpha;
+  h->beta0 = beta;
+  cd_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  if (h->opt.max_batch < 1 || h->opt.max_batch > 4096 || h->opt.chunk < 1 || h->opt.maxit < 1 ||
+      !(h->opt.rtol > 0) || h->opt.precond < 0 || h->opt.precond > 3 || h->opt.precision < 0 ||
+      h->opt.precision > 1) {
+    set_error("invalid options");
+    return CD_EINVAL;
+  }
+  h->s = static_cast<cudaStream_t>(stream);
+  if (prepare_kernels() != 0) {
+    set_error(cudaGetErrorString(cudaGetLastError()));
+    return CD_ECUDA;
+  }
+  h->N = (long long)cd_dofs(d, p, n);
+  h->Bcap = h->opt.max_batch;
+  const int B = h->Bcap;
+  const long long N = h->N;
+  const int m = h->m, P = h->P, W = 2 * P + 1;
+  // 1D bands on every level (finest: quadrature; coarser: Galerkin P^T X P)
+  Band M, A, S;
+  iga_bands(p, n, P, M, A, S);
+  const int m_min = std::max(1, h->opt.mg_m_min);
+  for (;;) {
+    h->hM.push_back(M);
+    h->hA.push_back(A);
+    h->hS.push_back(S);
+    h->ml.push_back(M.m);
+    if (M.m <= m_min || M.m / 2 < 1) break;
+    M = coarsen(M);
+    A = coarsen(A);
+    S = coarsen(S);
+  }
+  std::vector<double> all;
+  for (size_t l = 0; l < h->ml.size(); ++l) {
+    h->boff.push_back(all.size());
+    all.insert(all.end(), h->hM[l].v.begin(), h->hM[l].v.end());
+    all.insert(all.end(), h->hA[l].v.begin(), h->hA[l].v.end());
+    all.insert(all.end(), h->hS[l].v.begin(), h->hS[l].v.end());
+  }
+  (void)W;
+  if (upload(h->bands64, all) != cudaSuccess || upload(h->bands32, cast_vec<float>(all)) != cudaSuccess) {
+    set_error("band upload failed");
+    return CD_ECUDA;
+  }
+  // FD eigenbases of the finest level
+  {
+    std::vector<double> Md = band_to_dense(h->hM[0]), Sd = band_to_dense(h->hS[0]);
+    if (!gen_eig(m, Md, Sd, h->UD, h->lamD)) {
+      set_error("generalized eigen-decomposition failed");
+      return CD_EINVAL;
+    }
+    Band T;
+    toeplitz_T_band(p, m, P, T);
+    std::vector<double> Td = band_to_dense(T);
+    sym_eig(m, Td, h->UT, h->lamT);
+    auto transpose = [m](const std::vector<double>& U) {
+      std::vector<double> t((size_t)m * m);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) t[(size_t)j * m + i] = U[(size_t)i * m + j];
+      return t;
+    };
+    std::vector<double> UDt = transpose(h->UD), UTt = transpose(h->UT);
+    bool ok = upload(h->UD64, h->UD) == cudaSuccess && upload(h->UDt64, UDt) == cudaSuccess &&
+              upload(h->lamD64, h->lamD) == cudaSuccess && upload(h->UT64, h->UT) == cudaSuccess &&
+              upload(h->UTt64, UTt) == cudaSuccess && upload(h->lamT64, h->lamT) == cudaSuccess &&
+              upload(h->UD32, cast_vec<float>(h->UD)) == cudaSuccess &&
+              upload(h->UDt32, cast_vec<float>(UDt)) == cudaSuccess &&
+              upload(h->lamD32, cast_vec<float>(h->lamD)) == cudaSuccess &&
+              upload(h->UT32, cast_vec<float>(h->UT)) == cudaSuccess &&
+              upload(h->UTt32, cast_vec<float>(UTt)) == cudaSuccess &&
+              upload(h->lamT32, cast_vec<float>(h->lamT)) == cudaSuccess;
+    if (!ok) {
+      set_error("eigenbasis upload failed");
+      return CD_ECUDA;
+    }
+    h->have_fd = true;
+  }
+  // workspace
+  auto al = [&](DevBuf& bfr, size_t bytes) { return bfr.alloc(bytes) == cudaSuccess; };
+  bool ok = al(h->alpha, 8 * B) && al(h->beta, 8 * B);
+  for (auto& x : h->sd) ok = ok && al(x, 8 * B);
+  for (auto& x : h->si) ok = ok && al(x, 4 * B);
+  for (auto& x : h->part) ok = ok && al(x, 8 * (size_t)B * 1024);
+  ok = ok && al(h->ir_rnorm, 8 * B) && al(h->ir_bnorm2, 8 * B) && al(h->ir_relres, 8 * B) &&
+       al(h->ir_active, 4 * B) && al(h->ir_status, 4 * B) && al(h->ir_outer, 4 * B) &&
+       al(h->ir_inner_total, 4 * B) && al(h->cnt, 64) && al(h->r64, 8 * (size_t)B * N);
+  const long long scratch3d = (d == 3) ? 21LL * (N / 3) * B : 0;
+  for (int prec = 0; prec < 2; ++prec) {
+    const size_t es = prec == 0 ? 8 : 4;
+    Workspace& w = prec == 0 ? h->w64 : h->w32;
+    const size_t vb = es * (size_t)B * N;
+    ok = ok && al(w.x, vb) && al(w.r, vb) && al(w.z, vb) && al(w.p, vb) && al(w.q, vb) &&
+         al(w.fa, vb) && al(w.fb, vb) && al(w.apply_scratch, es * (size_t)std::max<long long>(scratch3d, 1));
+  }
+  if (!ok) {
+    set_error("workspace allocation failed");
+    cudaGetLastError();
+    return CD_ENOMEM;
+  }
+  if (cudaMallocHost(&h->h_cnt, 64) != cudaSuccess) return CD_ENOMEM;
+  {
+    cd_status st = mg_build(h->mg, d, P, h->ml, h->hM, h->hA, h->hS, B,
+                            std::max(1, h->opt.smoother_degree), h->bands64.as<double>(),
+                            h->bands32.as<float>(), h->boff);
+    if (st != CD_OK) return st;
+  }
+  if (cudaStreamSynchronize(h->s) != cudaSuccess) {
+    set_error(cudaGetErrorString(cudaGetLastError()));
+    return CD_ECUDA;
+  }
+  *out = h.release();
+  return CD_OK;
+}
+
+cd_status cd_destroy(cd_solver h) {
+  if (!h) return CD_EINVAL;
+  cudaStreamSynchronize(h->s);
+  delete h;
+  return CD_OK;
+}
+
+static cd_status check_call(cd_solver h, const void* a, const void* b, int nrhs) {
+  if (!h || !a || !b) {
+    set_error("NULL argument");
+    return CD_EINVAL;
+  }
+  if (nrhs < 1 || nrhs > h->Bcap) {
+    set_error("nrhs out of range [1, max_batch]");
+    return CD_EINVAL;
+  }
+  return CD_OK;
+}
+
+cd_status cd_apply(cd_solver h, const double* w, double* y, int nrhs, const double* alphas,
+                   const double* betas) {
+  cd_status st = check_call(h, w, y, nrhs);
+  if (st != CD_OK) return st;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
+  apply_level<double>(h, 0, w, y, nullptr, 0, nrhs, nullptr, nullptr, nullptr);
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+cd_status cd_apply_f32(cd_solver h, const float* w, float* y, int nrhs, const double* alphas,
+                       const double* betas) {
+  cd_status st = check_call(h, w, y, nrhs);
+  if (st != CD_OK) return st;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
+  apply_level<float>(h, 0, w, y, nullptr, 0, nrhs, nullptr, nullptr, nullptr);
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+cd_status cd_solve(cd_solver h, const double* b, double* x, int nrhs, const double* alphas,
+                   const double* betas, cd_result* res) {
+  cd_status st = check_call(h, b, x, nrhs);
+  if (st != CD_OK) return st;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
+  return solve_device(h, b, x, nrhs, res);
+}
+
+cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int nrhs,
+                        const double* alphas, const double* betas, cd_result* res) {
+  cd_status st = check_call(h, b_host, x_host, nrhs);
+  if (st != CD_OK) return st;
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
+  const size_t bytes = 8 * (size_t)nrhs * h->N;
+  if (!h->b64.p) {
+    if (h->b64.alloc(8 * (size_t)h->Bcap * h->N) != cudaSuccess ||
+        h->x64.alloc(8 * (size_t)h->Bcap * h->N) != cudaSuccess)
+      return CD_ENOMEM;
+  }
+  CD_CUDA_OK(cudaMemcpyAsync(h->b64.p, b_host, bytes, cudaMemcpyHostToDevice, h->s));
+  st = solve_device(h, h->b64.as<double>(), h->x64.as<double>(), nrhs, res);
+  if (st != CD_OK && st != CD_NOT_CONVERGED && st != CD_BREAKDOWN) return st;
+  CD_CUDA_OK(cudaMemcpyAsync(x_host, h->x64.p, bytes, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaStreamSynchronize(h->s));
+  return st;
+}
+
+cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs, const double* alphas,
+                     const double* betas, int f32) {
+  cd_status st = check_call(h, r, z, nrhs);
+  if (st != CD_OK) return st;
+  if (kind < CD_PC_NONE || kind > CD_PC_MG) return CD_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  const int keep = h->opt.precond;
+  h->opt.precond = kind;  // so that set_params prepares the MG coarse data when needed
+  st = set_params(h, nrhs, alphas, betas);
+  h->opt.precond = keep;
+  if (st != CD_OK) return st;
+  if (f32)
+    apply_prec<float>(h, kind, nrhs, (const float*)r, (float*)z, nullptr);
+  else
+    apply_prec<double>(h, kind, nrhs, (const double*)r, (double*)z, nullptr);
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+int cd_levels(cd_solver h) { return h ? (int)h->ml.size() : 0; }
+
+cd_status cd_get_bands(cd_solver h, int level, double* M, double* A, double* S, int* m_out,
+                       int* P_out) {
+  if (!h || level < 0 || level >= (int)h->ml.size()) return CD_EINVAL;
+  if (m_out) *m_out = h->ml[level];
+  if (P_out) *P_out = h->P;
+  const size_t n = h->hM[level].v.size();
+  if (M) std::memcpy(M, h->hM[level].v.data(), n * 8);
+  if (A) std::memcpy(A, h->hA[level].v.data(), n * 8);
+  if (S) std::memcpy(S, h->hS[level].v.data(), n * 8);
+  return CD_OK;
+}
+
+cd_status cd_get_eig(cd_solver h, int which, double* U, double* lam) {
+  if (!h || !h->have_fd || (which != 0 && which != 1)) return CD_EINVAL;
+  const std::vector<double>& Us = which == 0 ? h->UD : h->UT;
+  const std::vector<double>& ls = which == 0 ? h->lamD : h->lamT;
+  if (U) std::memcpy(U, Us.data(), Us.size() * 8);
+  if (lam) std::memcpy(lam, ls.data(), ls.size() * 8);
+  return CD_OK;
+}
+
+cd_status cd_restrict(cd_solver h, int level, const double* fine, double* coarse, int nrhs) {
+  cd_status st = check_call(h, fine, coarse, nrhs);
+  if (st != CD_OK) return st;
+  if (level < 0 || level + 1 >= (int)h->ml.size()) return CD_EINVAL;
+  mg_restrict<double>(h->d, h->ml[level], h->ml[level + 1], nrhs, fine, coarse, nullptr, h->s);
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+cd_status cd_prolong(cd_solver h, int level, const double* coarse, double* fine, int nrhs) {
+  cd_status st = check_call(h, coarse, fine, nrhs);
+  if (st != CD_OK) return st;
+  if (level < 0 || level + 1 >= (int)h->ml.size()) return CD_EINVAL;
+  mg_prolong_add<double>(h->d, h->ml[level], h->ml[level + 1], nrhs, coarse, fine, nullptr, h->s);
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+}  // extern "C"

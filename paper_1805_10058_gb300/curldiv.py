@@ -1,0 +1,226 @@
+"""Thin ctypes binding of the C-ABI in include/curldiv.h (argument marshalling only).
+
+Every computation runs in libcurldiv.so's CUDA kernels; there is no Python or CPU
+fallback.  Device vectors are passed as torch CUDA tensors (FP64 or FP32, contiguous),
+host vectors as numpy arrays.  Names follow the C entry points.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcurldiv.so")
+
+CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_NOT_CONVERGED, CD_BREAKDOWN, CD_TIMEOUT, CD_CANCELLED = range(8)
+CD_PREC_FP64, CD_PREC_FP32_IR = 0, 1
+CD_PC_NONE, CD_PC_FD_D, CD_PC_FD_T, CD_PC_MG = 0, 1, 2, 3
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("rtol", ctypes.c_double), ("max_batch", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
+                ("max_outer", ctypes.c_int), ("smoother_degree", ctypes.c_int),
+                ("mg_m_min", ctypes.c_int), ("use_graphs", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("iters_outer", ctypes.c_int), ("iters_inner", ctypes.c_int),
+                ("relres", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return dict(iters_outer=self.iters_outer, iters_inner=self.iters_inner,
+                    relres=self.relres, seconds=self.seconds, status=self.status)
+
+
+class CurlDivError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Loads libcurldiv.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp, i, d, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "cd_default_options": (None, [ctypes.POINTER(Options)]),
+        "cd_dofs": (ctypes.c_size_t, [i, i, i]),
+        "cd_strerror": (ctypes.c_char_p, [i]),
+        "cd_last_error": (ctypes.c_char_p, []),
+        "cd_create": (i, [ctypes.POINTER(vp), i, i, i, d, d, ctypes.POINTER(Options), vp]),
+        "cd_destroy": (i, [vp]),
+        "cd_apply": (i, [vp, vp, vp, i, dp, dp]),
+        "cd_apply_f32": (i, [vp, vp, vp, i, dp, dp]),
+        "cd_solve": (i, [vp, vp, vp, i, dp, dp, ctypes.POINTER(Result)]),
+        "cd_solve_host": (i, [vp, vp, vp, i, dp, dp, ctypes.POINTER(Result)]),
+        "cd_precond": (i, [vp, i, vp, vp, i, dp, dp, i]),
+        "cd_get_bands": (i, [vp, i, dp, dp, dp, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "cd_levels": (i, [vp]),
+        "cd_get_eig": (i, [vp, i, dp, dp]),
+        "cd_restrict": (i, [vp, i, vp, vp, i]),
+        "cd_prolong": (i, [vp, i, vp, vp, i]),
+        "cd_kernel_launches": (ctypes.c_uint64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st, what):
+    if st != CD_OK:
+        lib = load()
+        raise CurlDivError(st, f"{what}: {lib.cd_strerror(st).decode()} ({lib.cd_last_error().decode()})")
+
+
+def default_options(**kw):
+    o = Options()
+    load().cd_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def cd_dofs(d, p, n):
+    return int(load().cd_dofs(d, p, n))
+
+
+def cd_kernel_launches():
+    return int(load().cd_kernel_launches())
+
+
+def _params(nrhs, alphas, betas):
+    def arr(v):
+        if v is None:
+            return None, None
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (nrhs,)))
+        return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ka, pa = arr(alphas)
+    kb, pb = arr(betas)
+    return (ka, kb), pa, pb
+
+
+def _dev(t, dtype_name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"expected torch.{dtype_name}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """Owns a cd_solver handle for (d, p, n); methods mirror the C entry points."""
+
+    def __init__(self, d, p, n, alpha=1.0, beta=1.0, stream=None, **opts):
+        self.lib = load()
+        self.d, self.p, self.n = d, p, n
+        self.m = n + p - 2
+        self.N = cd_dofs(d, p, n)
+        self.opts = default_options(**opts)
+        h = ctypes.c_void_p()
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        _check(self.lib.cd_create(ctypes.byref(h), d, p, n, alpha, beta, ctypes.byref(self.opts),
+                                  ctypes.c_void_p(stream)), "cd_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cd_apply(self, w, y, alphas=None, betas=None):
+        nrhs = w.numel() // self.N
+        keep, pa, pb = _params(nrhs, alphas, betas)
+        _check(self.lib.cd_apply(self.h, _dev(w, "float64"), _dev(y, "float64"), nrhs, pa, pb), "cd_apply")
+
+    def cd_apply_f32(self, w, y, alphas=None, betas=None):
+        nrhs = w.numel() // self.N
+        keep, pa, pb = _params(nrhs, alphas, betas)
+        _check(self.lib.cd_apply_f32(self.h, _dev(w, "float32"), _dev(y, "float32"), nrhs, pa, pb),
+               "cd_apply_f32")
+
+    def cd_solve(self, b, x, alphas=None, betas=None, check=True):
+        nrhs = b.numel() // self.N
+        keep, pa, pb = _params(nrhs, alphas, betas)
+        res = (Result * nrhs)()
+        st = self.lib.cd_solve(self.h, _dev(b, "float64"), _dev(x, "float64"), nrhs, pa, pb, res)
+        if check and st not in (CD_OK,):
+            _check(st, "cd_solve")
+        return st, [r.as_dict() for r in res]
+
+    def cd_solve_host(self, b, x, alphas=None, betas=None):
+        assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+        nrhs = b.size // self.N
+        keep, pa, pb = _params(nrhs, alphas, betas)
+        res = (Result * nrhs)()
+        st = self.lib.cd_solve_host(self.h, ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(x.ctypes.data),
+                                    nrhs, pa, pb, res)
+        return st, [r.as_dict() for r in res]
+
+    def cd_precond(self, kind, r, z, alphas=None, betas=None):
+        f32 = str(r.dtype) == "torch.float32"
+        nrhs = r.numel() // self.N
+        keep, pa, pb = _params(nrhs, alphas, betas)
+        dt = "float32" if f32 else "float64"
+        _check(self.lib.cd_precond(self.h, kind, _dev(r, dt), _dev(z, dt), nrhs, pa, pb, int(f32)),
+               "cd_precond")
+
+    def cd_levels(self):
+        return int(self.lib.cd_levels(self.h))
+
+    def cd_get_bands(self, level=0):
+        m, P = ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.cd_get_bands(self.h, level, None, None, None, ctypes.byref(m), ctypes.byref(P)),
+               "cd_get_bands")
+        W = 2 * P.value + 1
+        arrs = [np.zeros((m.value, W)) for _ in range(3)]
+        ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+        _check(self.lib.cd_get_bands(self.h, level, ptr(arrs[0]), ptr(arrs[1]), ptr(arrs[2]),
+                                     ctypes.byref(m), ctypes.byref(P)), "cd_get_bands")
+        return arrs, P.value
+
+    def cd_get_eig(self, which):
+        U = np.zeros((self.m, self.m))
+        lam = np.zeros(self.m)
+        ptr = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+        _check(self.lib.cd_get_eig(self.h, which, ptr(U), ptr(lam)), "cd_get_eig")
+        return U, lam
+
+    def cd_restrict(self, level, fine, coarse):
+        nrhs = fine.numel() // (self.d * self.level_m(level) ** self.d)
+        _check(self.lib.cd_restrict(self.h, level, _dev(fine, "float64"), _dev(coarse, "float64"), nrhs),
+               "cd_restrict")
+
+    def cd_prolong(self, level, coarse, fine):
+        nrhs = fine.numel() // (self.d * self.level_m(level) ** self.d)
+        _check(self.lib.cd_prolong(self.h, level, _dev(coarse, "float64"), _dev(fine, "float64"), nrhs),
+               "cd_prolong")
+
+    def level_m(self, level):
+        m = self.m
+        for _ in range(level):
+            m //= 2
+        return m
