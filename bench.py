@@ -1,0 +1,343 @@
+"""Benchmark of the curl-div solve loop on GB300 (one JSON line on stdout, rank 0).
+
+Workload (one step): the 2D sweep -- p in {2, 3, 4}, n = 256 (m = n + p - 2 per axis,
+2 m^2 unknowns per solve), alpha = 1, beta in {1e-6, 1e-3, 1, 1e3, 1e6}, 8 seeded
+uniform[-1, 1] right-hand sides per (p, beta): 120 solves to relative residual 1e-10,
+multigrid-preconditioned flexible CG with FP32 inner solves inside FP64 refinement
+(FP64 Krylov + FP32 multigrid for the parameter ratios 1e6).  The 40 solves of one p
+form one batched call.  All right-hand sides are resident in HBM before timing; L2 is
+flushed (256 MB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the solves are independent, so N ranks run N replicas of the workload with
+no collective on the data path ("weak" scaling, value = solves of all ranks / max time).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s + p50/p99 latency at 1e-10 residual; operator-apply GB/s vs HBM peak"
+PS = (2, 3, 4)
+N_INT = 256
+BETAS = (1e-6, 1e-3, 1.0, 1e3, 1e6)
+SEEDS = tuple(range(8))
+RTOL = 1e-10
+WORKLOAD = ("2D curl-div sweep: p in {2,3,4}, n=256 (~131k-133k DoF/solve), alpha=1, "
+            "beta in {1e-6,1e-3,1,1e3,1e6}, 8 uniform[-1,1] RHS per case (120 solves), "
+            "MG-preconditioned FCG, FP32 inner + FP64 refinement, rtol 1e-10")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ reference (oracle) arm
+# The oracle's sparse direct solve takes minutes per n = 256 system and its CG needs
+# 10^4+ iterations below beta = 1e-3, so the CPU arm times a bounded sample: the paper's
+# plain CG (oracle.solvers.cg, FP64) at beta = 1, one right-hand side, cycling over p.
+REF_SAMPLE = "oracle plain CG (FP64, Section 6.2 CG) to rtol 1e-10 at beta=1, one uniform RHS per solve, cycling p in {2,3,4}; the easiest case of the sweep"
+
+
+def oracle_solve(p, seed):
+    from oracle import assemble, solvers
+    from paper_1805_10058_gb300 import inputs
+    b = inputs.uniform_rhs(2, p, N_INT, seed=seed)[0]
+    A = assemble.galerkin_kron(2, p, N_INT, 1.0, 1.0)
+    x, k, _ = solvers.cg(A, b, RTOL, 100000)
+    rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+    assert rel <= 1.01 * RTOL, rel
+    return k
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    times = []
+    for it in range(args.warmup + args.steps):
+        p = PS[it % len(PS)]
+        t0 = time.perf_counter()
+        oracle_solve(p, seed=it)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "step": REF_SAMPLE},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} solves: {REF_SAMPLE}"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample():
+    """The oracle as it stands on a bounded sample (two solves, about 10 s)."""
+    t0 = time.perf_counter()
+    for p in (2, 3):
+        oracle_solve(p, seed=1)
+    dt = time.perf_counter() - t0
+    return {"value": 2 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"2 solves (p=2,3): {REF_SAMPLE}; {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1805_10058_gb300 import curldiv as cdl
+    from paper_1805_10058_gb300 import inputs
+
+    stream = torch.cuda.current_stream(dev)
+    streams = [torch.cuda.Stream(dev) for _ in PS]  # one stream (and host thread) per shape
+    prec = cdl.CD_PREC_FP64 if args.precision == "fp64" else cdl.CD_PREC_FP32_IR
+    pcs = {"mg": cdl.CD_PC_MG, "fdd": cdl.CD_PC_FD_D, "none": cdl.CD_PC_NONE}
+    B = len(BETAS) * len(SEEDS)
+    solvers_, rhs, xs, alph, bet, rhs_host = [], [], [], [], [], []
+    for p in PS:
+        s = cdl.Solver(2, p, N_INT, max_batch=B, precond=pcs[args.precond], precision=prec,
+                       rtol=RTOL, maxit=args.maxit, stream=streams[len(solvers_)].cuda_stream)
+        solvers_.append(s)
+        bh = np.concatenate([inputs.uniform_rhs(2, p, N_INT, seed=sd)[0] for _ in BETAS for sd in SEEDS])
+        rhs_host.append(bh)
+        rhs.append(torch.as_tensor(bh, device=dev))
+        xs.append(torch.zeros_like(rhs[-1]))
+        alph.append(np.ones(B))
+        bet.append(np.repeat(BETAS, len(SEEDS)))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(record):
+        """One pass over the sweep: the three batched calls run concurrently, each on its own
+        stream from its own host thread; returns per-solve latencies from the step start."""
+        lat = [None] * len(solvers_)
+        out = [None] * len(solvers_)
+        t0 = time.perf_counter()
+
+        def run(i):
+            st, res = solvers_[i].cd_solve(rhs[i], xs[i], alph[i], bet[i], check=False)
+            out[i] = res
+            lat[i] = [time.perf_counter() - t0] * len(res)
+
+        ths = [threading.Thread(target=run, args=(i,)) for i in range(len(solvers_))]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        for r in out:
+            record.append(r)
+        return [v for l in lat for v in l]
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step([])
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    lat_all, recs, step_ms = [], [], []
+    launches0 = cdl.cd_kernel_launches()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat_all.extend(step(recs))
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        step_ms.append(ms)
+        total_ms += ms
+    launches = cdl.cd_kernel_launches() - launches0
+    clk = clocks.stop()
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_solves = len(PS) * B * args.steps
+    value = ws * n_solves / (total_ms / 1e3)
+    flat = [r for step_res in recs for r in step_res]
+    ok = sum(1 for r in flat if r["status"] == 0)
+    worst = max(r["relres"] for r in flat)
+    iters = [r["iters_inner"] for r in flat]
+
+    # e2e: the same workload through the host-buffer entry point (copies inside)
+    xh = [np.zeros_like(bh) for bh in rhs_host]
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+
+    def run_host(i):
+        solvers_[i].cd_solve_host(rhs_host[i], xh[i], alph[i], bet[i])
+
+    ths = [threading.Thread(target=run_host, args=(i,)) for i in range(len(solvers_))]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te0
+    h2d = sum(b.nbytes for b in rhs_host)
+
+    # roofline of the dominant kernel: the FP32 operator apply on the p = 3 batch (B = 40),
+    # CUDA events on the library stream, L2 flushed before each timed launch
+    hbm, peak_kind = peaks()
+    s = solvers_[1]
+    stream = streams[1]
+    w32 = torch.rand(B * s.N, dtype=torch.float32, device=dev)
+    y32 = torch.empty_like(w32)
+    for _ in range(3):
+        s.cd_apply_f32(w32, y32, alph[1], bet[1])
+    times = []
+    for _ in range(20):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.cd_apply_f32(w32, y32, alph[1], bet[1])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    t_apply = statistics.mean(times) / 1e3
+    alg_bytes = 2 * B * s.N * 4
+    achieved = alg_bytes / t_apply / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "apply_traffic.json")) as f:
+            tr = json.load(f)
+        if tr.get("kernel_version") == "apply2d_v1":
+            traffic = tr.get("bytes_per_launch")
+    except Exception:
+        pass
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec else "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "solves_per_step": len(PS) * B, "batch": B,
+                           "precond": args.precond, "precision": args.precision,
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": f"replicas x{ws}"},
+                "latency_s": {"p50": float(np.percentile(lat_all, 50)), "p99": float(np.percentile(lat_all, 99)),
+                              "definition": "per solve, from step start to the return of its batched call "
+                                            "(three shape batches run concurrently on three streams)"},
+                "solves": {"converged": ok, "total": len(flat), "worst_relres": worst,
+                           "iters_median": float(np.median(iters)), "iters_max": int(max(iters))},
+                "e2e": {"value": len(PS) * B / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": h2d},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                             "kernel": "apply2d_kernel<float> (p=3, n=256, batch 40)",
+                             "launch_us": t_apply * 1e6},
+                "gpu_launches": int(launches),
+                "clocks": clk}
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precond", default="mg", choices=["mg", "fdd", "none"])
+    ap.add_argument("--maxit", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

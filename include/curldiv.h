@@ -59,11 +59,18 @@ typedef enum {
   CD_CANCELLED = 7
 } cd_status;
 
-/* Arithmetic of the solve.
- * CD_PREC_FP64: every kernel in FP64 (operator, Krylov vectors, preconditioner).
- * CD_PREC_FP32_IR: FP64 iterative refinement (outer residual b - A x in FP64,
- *   x updated in FP64) around an inner preconditioned Krylov solve whose
- *   operator, vectors and preconditioner are FP32 (inner products in FP64). */
+/* Arithmetic of the solve.  Both modes run an outer loop that measures the true
+ * residual b - A x in FP64 and updates x in FP64; they differ in the inner solve.
+ * CD_PREC_FP64: every kernel in FP64 (operator, Krylov vectors, preconditioner); the
+ *   outer loop only restarts the Krylov solve when its recursive residual has
+ *   drifted from the true one.
+ * CD_PREC_FP32_IR: iterative refinement.  A right-hand side whose parameter ratio
+ *   max(alpha, beta) / min(alpha, beta) is below `mixed_switch_ratio` gets an inner
+ *   preconditioned Krylov solve whose operator, vectors and preconditioner are FP32
+ *   (inner products in FP64).  Above the ratio, or after an FP32 refinement step
+ *   that reduced the residual less than tenfold, its inner solve is FP64 throughout:
+ *   in FP32 the contribution of the small parameter to A w cancels below rounding
+ *   for the near-null fields of the large one, and refinement stalls or diverges. */
 enum { CD_PREC_FP64 = 0, CD_PREC_FP32_IR = 1 };
 
 /* Preconditioner of the Krylov solve.
@@ -90,6 +97,8 @@ typedef struct {
   int mg_m_min;       /* MG: stop coarsening at m <= mg_m_min (default 3)         */
   int use_graphs;     /* capture the Krylov iteration in CUDA graphs (default 1)  */
   int chunk;          /* iterations per graph launch / host convergence poll (8)  */
+  double mixed_switch_ratio; /* FP32-IR: parameter ratio above which the inner
+                                Krylov solve is FP64 (default 1e4)                 */
   int reserved[8];
 } cd_options;
 

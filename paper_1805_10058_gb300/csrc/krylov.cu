@@ -176,7 +176,7 @@ __global__ void cg_alpha_kernel(int B, PcgState st, const double* part_pq, int n
 }
 
 __global__ void cg_check_kernel(int B, PcgState st, const double* part_rr, int nrr,
-                                const double* part_rzold, int nrz, double tol2, int maxit) {
+                                const double* part_rzold, int nrz, const double* tol2v, int maxit) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || !st.active[b]) return;
   const double rr = psum(part_rr, nrr, b);
@@ -187,7 +187,7 @@ __global__ void cg_check_kernel(int B, PcgState st, const double* part_rr, int n
   if (!(rr == rr)) {
     st.status[b] = CD_BREAKDOWN;
     st.active[b] = 0;
-  } else if (rr <= tol2 * st.rr0[b]) {
+  } else if (rr <= tol2v[b] * st.rr0[b]) {
     st.status[b] = CD_OK;
     st.active[b] = 0;
   } else if (it >= maxit) {
@@ -221,27 +221,111 @@ __global__ void count_active_kernel(int B, const int* __restrict__ active, int* 
   if (threadIdx.x == 0) *out = s;
 }
 
-// IR outer step: rnorm = sqrt(rr); decide convergence against ||b||
+// Outer step of the refinement loop: rnorm = ||b - A x||; decide convergence against
+// ||b|| (or give up after max_outer steps / maxit Krylov iterations in total); move an
+// FP32-inner solve whose last step reduced the residual less than tenfold to the FP64
+// group; set the per-solve inner tolerance (squared).
 __global__ void ir_check_kernel(int B, const double* part_rr, int nrr, const double* bnorm2,
-                                double* rnorm, int* active, int* status, double* relres,
-                                int* outer_it, double tol2, int max_outer) {
+                                double* rnorm, double* rrprev, int* active, int* status,
+                                double* relres, int* outer_it, int* grp, double* tol2v,
+                                double tol2, double inner2, int max_outer,
+                                const int* inner_total, int maxit) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || !active[b]) return;
   const double rr = psum(part_rr, nrr, b);
   rnorm[b] = sqrt(rr);
   relres[b] = bnorm2[b] > 0 ? sqrt(rr / bnorm2[b]) : 0.0;
-  if (!(rr == rr)) {
+  if (!(rr == rr) || !(rr < 1e300)) {
     status[b] = CD_BREAKDOWN;
     active[b] = 0;
-  } else if (rr <= tol2 * bnorm2[b]) {
+    return;
+  }
+  if (rr <= tol2 * bnorm2[b]) {
     status[b] = CD_OK;
     active[b] = 0;
-  } else if (outer_it[b] >= max_outer) {
+    return;
+  }
+  if (outer_it[b] >= max_outer || inner_total[b] >= maxit) {
     status[b] = CD_NOT_CONVERGED;
     active[b] = 0;
-  } else {
-    outer_it[b] += 1;
+    return;
   }
+  if (outer_it[b] > 0 && grp[b] == 2 && rr > 0.25 * rrprev[b]) {
+    // an FP64 refinement step gained less than 2x: the FP64 attainable accuracy
+    // (about eps ||A|| ||x|| / ||b||) is reached
+    status[b] = CD_NOT_CONVERGED;
+    active[b] = 0;
+    return;
+  }
+  if (outer_it[b] > 0 && grp[b] == 0 && rr > 1e-2 * rrprev[b]) grp[b] = 2;
+  rrprev[b] = rr;
+  outer_it[b] += 1;
+  if (grp[b] == 0) {
+    tol2v[b] = inner2;
+  } else {
+    // aim at the final tolerance: rtol ||b|| relative to the current residual
+    double t = tol2 * bnorm2[b] / rr;
+    tol2v[b] = fmin(fmax(t, 1e-30), 0.25);
+  }
+}
+
+// masks of the three inner groups and their counts: out[g] = #{b : active && grp == g}
+__global__ void group_masks_kernel(int B, const int* active, const int* grp, int* m0, int* m1,
+                                   int* m2, int* out) {
+  __shared__ int c[4];
+  if (threadIdx.x < 4) c[threadIdx.x] = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const int a = active[b];
+    const int g = grp[b];
+    m0[b] = a && g == 0;
+    m1[b] = a && g == 1;
+    m2[b] = a && g == 2;
+    if (a) atomicAdd(&c[g], 1);
+    if (a) atomicAdd(&c[3], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) out[threadIdx.x] = c[threadIdx.x];
+}
+
+// dst = src / rnorm (FP64 inner right-hand side of unit norm)
+__global__ void __launch_bounds__(256) scale_div_kernel(long long N, const double* __restrict__ src,
+                                                        double* __restrict__ dst,
+                                                        const double* __restrict__ rnorm,
+                                                        const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const long long base = (long long)b * N;
+  const double s = 1.0 / rnorm[b];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[base + i] = src[base + i] * s;
+}
+
+// x64 += rnorm * e64
+__global__ void __launch_bounds__(256) ir_update64_kernel(long long N, double* __restrict__ x64,
+                                                          const double* __restrict__ e,
+                                                          const double* __restrict__ rnorm,
+                                                          const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const long long base = (long long)b * N;
+  const double s = rnorm[b];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    x64[base + i] += s * e[base + i];
+}
+
+template <typename S, typename D>
+__global__ void __launch_bounds__(256) convert_kernel(long long N, const S* __restrict__ src,
+                                                      D* __restrict__ dst,
+                                                      const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const long long base = (long long)b * N;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[base + i] = (D)src[base + i];
 }
 
 // ------------------------------------------------------------------ FD contraction
@@ -434,8 +518,8 @@ void cg_alpha(int B, PcgState st, const double* ppq, int npq, cudaStream_t s) {
   count_launch();
 }
 void cg_check(int B, PcgState st, const double* prr, int nrr, const double* prz, int nrz,
-              double tol2, int maxit, cudaStream_t s) {
-  cg_check_kernel<<<sgrid(B), 128, 0, s>>>(B, st, prr, nrr, prz, nrz, tol2, maxit);
+              const double* tol2v, int maxit, cudaStream_t s) {
+  cg_check_kernel<<<sgrid(B), 128, 0, s>>>(B, st, prr, nrr, prz, nrz, tol2v, maxit);
   count_launch();
 }
 void cg_beta(int B, PcgState st, const double* prz, int nrz, int flexible, cudaStream_t s) {
@@ -447,10 +531,35 @@ void count_active(int B, const int* active, int* out, cudaStream_t s) {
   count_launch();
 }
 void ir_check(int B, const double* prr, int nrr, const double* bnorm2, double* rnorm,
-              int* active, int* status, double* relres, int* outer_it, double tol2,
-              int max_outer, cudaStream_t s) {
-  ir_check_kernel<<<sgrid(B), 128, 0, s>>>(B, prr, nrr, bnorm2, rnorm, active, status, relres,
-                                           outer_it, tol2, max_outer);
+              double* rrprev, int* active, int* status, double* relres, int* outer_it, int* grp,
+              double* tol2v, double tol2, double inner2, int max_outer, const int* inner_total,
+              int maxit, cudaStream_t s) {
+  ir_check_kernel<<<sgrid(B), 128, 0, s>>>(B, prr, nrr, bnorm2, rnorm, rrprev, active, status,
+                                           relres, outer_it, grp, tol2v, tol2, inner2, max_outer,
+                                           inner_total, maxit);
+  count_launch();
+}
+void group_masks(int B, const int* active, const int* grp, int* m0, int* m1, int* m2, int* out,
+                 cudaStream_t s) {
+  group_masks_kernel<<<1, 256, 0, s>>>(B, active, grp, m0, m1, m2, out);
+  count_launch();
+}
+void scale_div(long long N, int B, const double* src, double* dst, const double* rnorm,
+               const int* active, cudaStream_t s) {
+  scale_div_kernel<<<vgrid(N, B), 256, 0, s>>>(N, src, dst, rnorm, active);
+  count_launch();
+}
+void ir_update64(long long N, int B, double* x64, const double* e, const double* rnorm,
+                 const int* active, cudaStream_t s) {
+  ir_update64_kernel<<<vgrid(N, B), 256, 0, s>>>(N, x64, e, rnorm, active);
+  count_launch();
+}
+void to_f32(long long N, int B, const double* src, float* dst, const int* active, cudaStream_t s) {
+  convert_kernel<double, float><<<vgrid(N, B), 256, 0, s>>>(N, src, dst, active);
+  count_launch();
+}
+void to_f64(long long N, int B, const float* src, double* dst, const int* active, cudaStream_t s) {
+  convert_kernel<float, double><<<vgrid(N, B), 256, 0, s>>>(N, src, dst, active);
   count_launch();
 }
 

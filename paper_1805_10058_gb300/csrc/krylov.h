@@ -54,11 +54,20 @@ void cg_init(int B, PcgState st, const double* prr, int nrr, const double* prz, 
              const int* outer_active, cudaStream_t s);
 void cg_alpha(int B, PcgState st, const double* ppq, int npq, cudaStream_t s);
 void cg_check(int B, PcgState st, const double* prr, int nrr, const double* prz, int nrz,
-              double tol2, int maxit, cudaStream_t s);
+              const double* tol2v, int maxit, cudaStream_t s);
 void cg_beta(int B, PcgState st, const double* prz, int nrz, int flexible, cudaStream_t s);
 void count_active(int B, const int* active, int* out, cudaStream_t s);
 void ir_check(int B, const double* prr, int nrr, const double* bnorm2, double* rnorm,
-              int* active, int* status, double* relres, int* outer_it, double tol2,
-              int max_outer, cudaStream_t s);
+              double* rrprev, int* active, int* status, double* relres, int* outer_it, int* grp,
+              double* tol2v, double tol2, double inner2, int max_outer, const int* inner_total,
+              int maxit, cudaStream_t s);
+void group_masks(int B, const int* active, const int* grp, int* m0, int* m1, int* m2, int* out,
+                 cudaStream_t s);
+void scale_div(long long N, int B, const double* src, double* dst, const double* rnorm,
+               const int* active, cudaStream_t s);
+void ir_update64(long long N, int B, double* x64, const double* e, const double* rnorm,
+                 const int* active, cudaStream_t s);
+void to_f32(long long N, int B, const double* src, float* dst, const int* active, cudaStream_t s);
+void to_f64(long long N, int B, const float* src, double* dst, const int* active, cudaStream_t s);
 
 }  // namespace cd

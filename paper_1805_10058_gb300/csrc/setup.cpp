@@ -2,6 +2,7 @@
 // bands, and small dense eigen-decompositions.  All of it is O(m p^2) or O(m^3) with
 // m <= a few hundred and runs once per (p, n); results are cached by the solver.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -13,11 +14,11 @@ namespace cd {
 
 // ------------------------------------------------------------------ errors / counters
 static thread_local std::string g_err;
-static thread_local uint64_t g_launches = 0;
+static std::atomic<uint64_t> g_launches{0};  // process-wide: solves may run on several threads
 void set_error(const std::string& msg) { g_err = msg; }
 const char* last_error() { return g_err.c_str(); }
-void count_launch(int k) { g_launches += (uint64_t)k; }
-uint64_t launches() { return g_launches; }
+void count_launch(int k) { g_launches.fetch_add((uint64_t)(int64_t)k, std::memory_order_relaxed); }
+uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 // ------------------------------------------------------------------ quadrature
 // Gauss-Legendre nodes on [-1, 1] by Newton iteration on the Legendre polynomial of

@@ -81,12 +81,14 @@ struct cd_solver_s {
   DevBuf si[3];  // active iters status
   DevBuf part[4];
   DevBuf ir_rnorm, ir_bnorm2, ir_relres, ir_active, ir_status, ir_outer, ir_inner_total, cnt;
+  DevBuf ir_rrprev, ir_grp, ir_tol2, ir_m0, ir_m1, ir_m2;
   DevBuf b64, x64, r64;
   Workspace w64, w32;
   int* h_cnt = nullptr;  // pinned
   MgData mg;
+  std::vector<double> mg_alpha, mg_beta;  // parameters the multigrid data was prepared for
   // CUDA graphs of a chunk of PCG iterations, keyed by (f32, B, pc, flexible, tol, maxit)
-  std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, uint64_t>> graphs;
+  std::map<std::tuple<int, int, int, int, int, int>, std::pair<cudaGraphExec_t, uint64_t>> graphs;
   std::mutex mu;
   ~cd_solver_s() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
@@ -183,7 +185,7 @@ static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* 
 
 // One PCG iteration (all kernels masked by the per-solve active flags).
 template <typename T>
-static void pcg_iteration(cd_solver h, int B, int pc, int flexible, double tol2, int maxit) {
+static void pcg_iteration(cd_solver h, int B, int pc, int flexible, const double* tol2v, int maxit) {
   Workspace& w = ws_of<T>(h);
   PcgState st = state_of(h);
   const long long N = h->N;
@@ -196,7 +198,7 @@ static void pcg_iteration(cd_solver h, int B, int pc, int flexible, double tol2,
                flexible ? w.z.as<T>() : nullptr, st.alpha, st.active, h->part[1].as<double>(),
                h->part[2].as<double>(), h->s);
   cg_check(B, st, h->part[1].as<double>(), nb, flexible ? h->part[2].as<double>() : nullptr, nb,
-           tol2, maxit, h->s);
+           tol2v, maxit, h->s);
   apply_prec<T>(h, pc, B, w.r.as<T>(), w.z.as<T>(), st.active);
   launch_dot<T>(w.r.as<T>(), w.z.as<T>(), N, B, h->part[3].as<double>(), nb, st.active, h->s);
   cg_beta(B, st, h->part[3].as<double>(), nb, flexible, h->s);
@@ -206,7 +208,7 @@ static void pcg_iteration(cd_solver h, int B, int pc, int flexible, double tol2,
 // Runs PCG on the workspace of precision T: r holds the right-hand side on entry, x the
 // solution on exit (x_0 = 0).  outer_active masks the solves that take part.
 template <typename T>
-static cd_status run_pcg(cd_solver h, int B, int pc, double tol, int maxit,
+static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int maxit,
                          const int* outer_active) {
   Workspace& w = ws_of<T>(h);
   PcgState st = state_of(h);
@@ -219,12 +221,11 @@ static cd_status run_pcg(cd_solver h, int B, int pc, double tol, int maxit,
   launch_dot<T>(w.r.as<T>(), w.z.as<T>(), N, B, h->part[3].as<double>(), nb, outer_active, h->s);
   cg_init(B, st, h->part[1].as<double>(), nb, h->part[3].as<double>(), nb, outer_active, h->s);
   vcopy<T>(N, B, w.z.as<T>(), w.p.as<T>(), st.active, h->s);
-  const double tol2 = tol * tol;
   const int chunk = std::max(1, h->opt.chunk);
   cudaGraphExec_t exec = nullptr;
   uint64_t nodes = 0;
   if (h->opt.use_graphs) {
-    auto key = std::make_tuple((int)(sizeof(T) == 4), B, pc, flexible, tol, maxit);
+    auto key = std::make_tuple((int)(sizeof(T) == 4), B, pc, flexible, 0, maxit);
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
       exec = it->second.first;
@@ -233,7 +234,7 @@ static cd_status run_pcg(cd_solver h, int B, int pc, double tol, int maxit,
       cudaGraph_t g = nullptr;
       const uint64_t c0 = launches();
       if (cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2, maxit);
+        for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2v, maxit);
         count_active(B, st.active, h->cnt.as<int>(), h->s);
         if (cudaStreamEndCapture(h->s, &g) == cudaSuccess && g) {
           if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
@@ -251,7 +252,7 @@ static cd_status run_pcg(cd_solver h, int B, int pc, double tol, int maxit,
       CD_CUDA_OK(cudaGraphLaunch(exec, h->s));
       count_launch((int)nodes);
     } else {
-      for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2, maxit);
+      for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2v, maxit);
       count_active(B, st.active, h->cnt.as<int>(), h->s);
     }
     CD_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->cnt.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
@@ -303,7 +304,9 @@ static cd_status final_residual(cd_solver h, int B, const double* b, const doubl
   return CD_OK;
 }
 
-static cd_status set_params(cd_solver h, int nrhs, const double* alphas, const double* betas) {
+static cd_status set_params(cd_solver h, int nrhs, const double* alphas, const double* betas,
+                            std::vector<double>* pa = nullptr, std::vector<double>* pb = nullptr,
+                            bool need_mg = false) {
   std::vector<double> a(nrhs), b(nrhs);
   for (int i = 0; i < nrhs; ++i) {
     a[i] = alphas ? alphas[i] : h->alpha0;
@@ -315,61 +318,89 @@ static cd_status set_params(cd_solver h, int nrhs, const double* alphas, const d
   }
   CD_CUDA_OK(cudaMemcpyAsync(h->alpha.p, a.data(), nrhs * 8, cudaMemcpyHostToDevice, h->s));
   CD_CUDA_OK(cudaMemcpyAsync(h->beta.p, b.data(), nrhs * 8, cudaMemcpyHostToDevice, h->s));
-  if (h->opt.precond == CD_PC_MG) {
+  CD_CUDA_OK(cudaStreamSynchronize(h->s));  // a, b are stack vectors
+  if (pa) *pa = a;
+  if (pb) *pb = b;
+  if (need_mg && (a != h->mg_alpha || b != h->mg_beta)) {
     cd_status st = mg_set_params(h->mg, h->d, h->P, nrhs, a, b, h->s);
     if (st != CD_OK) return st;
-    return mg_prepare(h->mg, nrhs, coef_of(h), h->w64.apply_scratch.as<double>(), h->s);
+    st = mg_prepare(h->mg, nrhs, coef_of(h), h->w64.apply_scratch.as<double>(), h->s);
+    if (st != CD_OK) return st;
+    h->mg_alpha = a;  // Chebyshev bounds and coarse inverses now match these parameters
+    h->mg_beta = b;
   }
   return CD_OK;
 }
 
-static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd_result* res) {
+static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd_result* res,
+                              const std::vector<double>& alphas, const std::vector<double>& betas) {
   auto t0 = std::chrono::steady_clock::now();
   const long long N = h->N;
   const int pc = h->opt.precond;
   std::vector<int> status(B, CD_OK), inner(B, 0), outer(B, 1);
-  if (h->opt.precision == CD_PREC_FP64) {
-    vcopy<double>(N, B, b, h->w64.r.as<double>(), nullptr, h->s);
-    cd_status st = run_pcg<double>(h, B, pc, h->opt.rtol, h->opt.maxit, nullptr);
-    if (st != CD_OK) return st;
-    vcopy<double>(N, B, h->w64.x.as<double>(), x, nullptr, h->s);
-    CD_CUDA_OK(cudaMemcpyAsync(status.data(), h->si[2].p, B * 4, cudaMemcpyDeviceToHost, h->s));
-    CD_CUDA_OK(cudaMemcpyAsync(inner.data(), h->si[1].p, B * 4, cudaMemcpyDeviceToHost, h->s));
-  } else {
-    // FP64 iterative refinement around FP32 inner PCG
-    const int nb = partial_blocks(N);
-    int* act = h->ir_active.as<int>();
-    set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, act, 1);
-    set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_status.as<int>(), CD_NOT_CONVERGED);
-    set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_outer.as<int>(), 0);
-    set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_inner_total.as<int>(), 0);
-    count_launch(4);
-    vzero<double>(N, B, x, nullptr, h->s);
-    launch_dot<double>(b, b, N, B, h->part[1].as<double>(), nb, nullptr, h->s);
-    launch_sum_partials(h->part[1].as<double>(), nb, B, h->ir_bnorm2.as<double>(), h->s);
-    for (int step = 0; step <= h->opt.max_outer + 1; ++step) {
-      int npart = 0;
-      apply_level<double>(h, 0, x, h->r64.as<double>(), b, 1, B, h->part[0].as<double>(), &npart,
-                          act);
-      ir_check(B, h->part[0].as<double>(), npart, h->ir_bnorm2.as<double>(),
-               h->ir_rnorm.as<double>(), act, h->ir_status.as<int>(), h->ir_relres.as<double>(),
-               h->ir_outer.as<int>(), h->opt.rtol * h->opt.rtol, h->opt.max_outer, h->s);
-      count_active(B, act, h->cnt.as<int>(), h->s);
-      CD_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->cnt.p, 4, cudaMemcpyDeviceToHost, h->s));
-      CD_CUDA_OK(cudaStreamSynchronize(h->s));
-      if (*h->h_cnt == 0) break;
-      ir_cast(N, B, h->r64.as<double>(), h->w32.r.as<float>(), h->ir_rnorm.as<double>(), act, h->s);
-      cd_status st = run_pcg<float>(h, B, pc, h->opt.inner_rtol, h->opt.inner_maxit, act);
+  // inner precision group per solve: 0 = FP32 Krylov + FP32 preconditioner, 2 = all FP64
+  // (group 1 is unused: an FP32 preconditioner inside FP64 Krylov was measured to need
+  // several times more iterations than FP64 throughout at parameter ratios of 1e6)
+  std::vector<int> grp(B, 2);
+  if (h->opt.precision == CD_PREC_FP32_IR)
+    for (int i = 0; i < B; ++i) {
+      const double ratio = std::max(alphas[i], betas[i]) / std::min(alphas[i], betas[i]);
+      grp[i] = ratio >= h->opt.mixed_switch_ratio ? 2 : 0;
+    }
+  const int nb = partial_blocks(N);
+  int* act = h->ir_active.as<int>();
+  int* m[3] = {h->ir_m0.as<int>(), h->ir_m1.as<int>(), h->ir_m2.as<int>()};
+  CD_CUDA_OK(cudaMemcpyAsync(h->ir_grp.p, grp.data(), B * 4, cudaMemcpyHostToDevice, h->s));
+  set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, act, 1);
+  set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_status.as<int>(), CD_NOT_CONVERGED);
+  set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_outer.as<int>(), 0);
+  set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_inner_total.as<int>(), 0);
+  count_launch(4);
+  vzero<double>(N, B, x, nullptr, h->s);
+  launch_dot<double>(b, b, N, B, h->part[1].as<double>(), nb, nullptr, h->s);
+  launch_sum_partials(h->part[1].as<double>(), nb, B, h->ir_bnorm2.as<double>(), h->s);
+  const double inner2 = h->opt.inner_rtol * h->opt.inner_rtol;
+  const double* tol2v = h->ir_tol2.as<double>();
+  for (int step = 0; step <= h->opt.max_outer + 1; ++step) {
+    int npart = 0;
+    apply_level<double>(h, 0, x, h->r64.as<double>(), b, 1, B, h->part[0].as<double>(), &npart,
+                        act);
+    ir_check(B, h->part[0].as<double>(), npart, h->ir_bnorm2.as<double>(), h->ir_rnorm.as<double>(),
+             h->ir_rrprev.as<double>(), act, h->ir_status.as<int>(), h->ir_relres.as<double>(),
+             h->ir_outer.as<int>(), h->ir_grp.as<int>(), h->ir_tol2.as<double>(),
+             h->opt.rtol * h->opt.rtol, inner2, h->opt.max_outer, h->ir_inner_total.as<int>(),
+             h->opt.maxit, h->s);
+    group_masks(B, act, h->ir_grp.as<int>(), m[0], m[1], m[2], h->cnt.as<int>(), h->s);
+    CD_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->cnt.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaStreamSynchronize(h->s));
+    int cnt[4] = {h->h_cnt[0], h->h_cnt[1], h->h_cnt[2], h->h_cnt[3]};
+    if (cnt[3] == 0) break;
+    if (cnt[0] > 0) {
+      ir_cast(N, B, h->r64.as<double>(), h->w32.r.as<float>(), h->ir_rnorm.as<double>(), m[0], h->s);
+      cd_status st = run_pcg<float>(h, B, pc, tol2v, h->opt.inner_maxit, m[0]);
       if (st != CD_OK) return st;
-      add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), act,
+      add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), m[0],
                                                           h->ir_inner_total.as<int>());
       count_launch();
-      ir_update(N, B, x, h->w32.x.as<float>(), h->ir_rnorm.as<double>(), act, h->s);
+      ir_update(N, B, x, h->w32.x.as<float>(), h->ir_rnorm.as<double>(), m[0], h->s);
     }
-    CD_CUDA_OK(cudaMemcpyAsync(status.data(), h->ir_status.p, B * 4, cudaMemcpyDeviceToHost, h->s));
-    CD_CUDA_OK(cudaMemcpyAsync(inner.data(), h->ir_inner_total.p, B * 4, cudaMemcpyDeviceToHost, h->s));
-    CD_CUDA_OK(cudaMemcpyAsync(outer.data(), h->ir_outer.p, B * 4, cudaMemcpyDeviceToHost, h->s));
+    for (int g = 1; g <= 2; ++g) {
+      if (cnt[g] == 0) continue;
+      scale_div(N, B, h->r64.as<double>(), h->w64.r.as<double>(), h->ir_rnorm.as<double>(), m[g], h->s);
+      // the first FP64 inner solve may use the whole budget; restarts after a drifted
+      // recursive residual are capped like FP32 inner solves
+      const int cap = step == 0 ? h->opt.maxit : std::min(h->opt.maxit, h->opt.inner_maxit);
+      cd_status st = run_pcg<double>(h, B, pc, tol2v, cap, m[g]);
+      if (st != CD_OK) return st;
+      add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), m[g],
+                                                          h->ir_inner_total.as<int>());
+      count_launch();
+      ir_update64(N, B, x, h->w64.x.as<double>(), h->ir_rnorm.as<double>(), m[g], h->s);
+    }
   }
+  CD_CUDA_OK(cudaMemcpyAsync(status.data(), h->ir_status.p, B * 4, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(inner.data(), h->ir_inner_total.p, B * 4, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(outer.data(), h->ir_outer.p, B * 4, cudaMemcpyDeviceToHost, h->s));
   std::vector<double> rel;
   cd_status st = final_residual(h, B, b, x, rel);
   if (st != CD_OK) return st;
@@ -410,6 +441,7 @@ void cd_default_options(cd_options* o) {
   o->mg_m_min = 3;
   o->use_graphs = 1;
   o->chunk = 8;
+  o->mixed_switch_ratio = 1e4;
 }
 
 size_t cd_dofs(int d, int p, int n) {
@@ -541,7 +573,9 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   for (auto& x : h->part) ok = ok && al(x, 8 * (size_t)B * 1024);
   ok = ok && al(h->ir_rnorm, 8 * B) && al(h->ir_bnorm2, 8 * B) && al(h->ir_relres, 8 * B) &&
        al(h->ir_active, 4 * B) && al(h->ir_status, 4 * B) && al(h->ir_outer, 4 * B) &&
-       al(h->ir_inner_total, 4 * B) && al(h->cnt, 64) && al(h->r64, 8 * (size_t)B * N);
+       al(h->ir_inner_total, 4 * B) && al(h->cnt, 64) && al(h->r64, 8 * (size_t)B * N) &&
+       al(h->ir_rrprev, 8 * B) && al(h->ir_grp, 4 * B) && al(h->ir_tol2, 8 * B) &&
+       al(h->ir_m0, 4 * B) && al(h->ir_m1, 4 * B) && al(h->ir_m2, 4 * B);
   const long long scratch3d = (d == 3) ? 21LL * (N / 3) * B : 0;
   for (int prec = 0; prec < 2; ++prec) {
     const size_t es = prec == 0 ? 8 : 4;
@@ -616,8 +650,9 @@ cd_status cd_solve(cd_solver h, const double* b, double* x, int nrhs, const doub
   cd_status st = check_call(h, b, x, nrhs);
   if (st != CD_OK) return st;
   std::lock_guard<std::mutex> lk(h->mu);
-  if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
-  return solve_device(h, b, x, nrhs, res);
+  std::vector<double> va, vb;
+  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond == CD_PC_MG)) != CD_OK) return st;
+  return solve_device(h, b, x, nrhs, res, va, vb);
 }
 
 cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int nrhs,
@@ -625,7 +660,8 @@ cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int n
   cd_status st = check_call(h, b_host, x_host, nrhs);
   if (st != CD_OK) return st;
   std::lock_guard<std::mutex> lk(h->mu);
-  if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
+  std::vector<double> va, vb;
+  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond == CD_PC_MG)) != CD_OK) return st;
   const size_t bytes = 8 * (size_t)nrhs * h->N;
   if (!h->b64.p) {
     if (h->b64.alloc(8 * (size_t)h->Bcap * h->N) != cudaSuccess ||
@@ -633,7 +669,7 @@ cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int n
       return CD_ENOMEM;
   }
   CD_CUDA_OK(cudaMemcpyAsync(h->b64.p, b_host, bytes, cudaMemcpyHostToDevice, h->s));
-  st = solve_device(h, h->b64.as<double>(), h->x64.as<double>(), nrhs, res);
+  st = solve_device(h, h->b64.as<double>(), h->x64.as<double>(), nrhs, res, va, vb);
   if (st != CD_OK && st != CD_NOT_CONVERGED && st != CD_BREAKDOWN) return st;
   CD_CUDA_OK(cudaMemcpyAsync(x_host, h->x64.p, bytes, cudaMemcpyDeviceToHost, h->s));
   CD_CUDA_OK(cudaStreamSynchronize(h->s));
@@ -646,10 +682,7 @@ cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs, co
   if (st != CD_OK) return st;
   if (kind < CD_PC_NONE || kind > CD_PC_MG) return CD_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
-  const int keep = h->opt.precond;
-  h->opt.precond = kind;  // so that set_params prepares the MG coarse data when needed
-  st = set_params(h, nrhs, alphas, betas);
-  h->opt.precond = keep;
+  st = set_params(h, nrhs, alphas, betas, nullptr, nullptr, kind == CD_PC_MG);
   if (st != CD_OK) return st;
   if (f32)
     apply_prec<float>(h, kind, nrhs, (const float*)r, (float*)z, nullptr);
