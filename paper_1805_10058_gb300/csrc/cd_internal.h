@@ -65,6 +65,14 @@ int launch_apply(int d, int m, int P, const T* bands /*M,A,S*/, const T* w, T* y
                  const T* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
                  const int* active, T* scratch, cudaStream_t s);
 
+// Central-stencil registry for the 2D apply: `bands_dev` is the start of a level's band
+// block ([3][m][W] row-major, then [3][W][m] k-major); rows [lo, hi) equal `central`
+// ([3][W]: M, A, S).
+void register_level(const void* bands_dev, int m, int P, int lo, int hi, const double* central);
+void unregister_level(const void* bands_dev);
+// 1 = Toeplitz-interior kernel (default), 0 = plain shared-memory kernel (kept for checks).
+void set_apply_variant(int v2);
+
 // Sets kernel attributes (dynamic shared memory caps); call once before launches/captures.
 int prepare_kernels();
 

@@ -16,6 +16,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
+#include <unordered_map>
 
 #include "cd_internal.h"
 
@@ -133,6 +135,228 @@ __global__ void __launch_bounds__(256) apply2d_kernel(int m, int P, int TR,
     const double s = block_sum(acc);
     if (threadIdx.x == 0) dotp[(size_t)b * gridDim.x + blockIdx.x] = s;
   }
+}
+
+// ------------------------------------------------------------------ 2D fused apply, v2
+// Rows lo..hi-1 of M, A and S equal the central Toeplitz stencil (Section 3.2: the central
+// entries are cardinal-spline values), which arrives as a kernel parameter (constant bank,
+// read straight into the FMAs); the ~2p boundary rows read the k-major band copy
+// bandT[X][k][i].  Phase A (axis x_1): each thread owns a column and keeps its TR + 2P
+// input rows in registers.  Phase B (axis x_2): each thread produces 4 consecutive
+// outputs from a register window over zero-padded shared-memory rows.
+template <typename T>
+struct Stencil {
+  T c[3][13];  // M, A, S central rows (k = 0..2P)
+  int lo, hi;  // rows [lo, hi) are Toeplitz
+};
+
+template <typename T, int P, int TR>
+__global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
+    int m, const T* __restrict__ bandT, Stencil<T> cs, const T* __restrict__ w,
+    T* __restrict__ y, const T* __restrict__ rhs, int mode, const double* __restrict__ alpha,
+    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp) {
+  constexpr int W = 2 * P + 1;
+  constexpr int NC = sizeof(T) == 8 ? 2 : 4;  // outputs per thread along x_2
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* su = reinterpret_cast<T*>(smem_raw);
+  const int ld = m + 2 * P;
+  const long long N = 2LL * m * m;
+  const T* w1 = w + (long long)b * N;
+  const T* w2 = w1 + (long long)m * m;
+  const int r0 = blockIdx.x * TR;
+  const int rows = min(TR, m - r0);
+  const T a = T(alpha[b]), be = T(beta[b]), g = T(alpha[b] - beta[b]);
+  const T* BM = bandT;
+  const T* BA = bandT + (size_t)W * m;
+  const T* BS = bandT + (size_t)2 * W * m;
+  const size_t plane = (size_t)TR * ld;
+  // ---- phase A: axis x_1
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    T in1[TR + 2 * P], in2[TR + 2 * P];
+#pragma unroll
+    for (int q = 0; q < TR + 2 * P; ++q) {
+      const int row = r0 - P + q;
+      const bool ok = row >= 0 && row < m;
+      in1[q] = ok ? w1[(long long)row * m + j] : T(0);
+      in2[q] = ok ? w2[(long long)row * m + j] : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r) {
+      if (r < rows) {
+        const int i = r0 + r;
+        T uM1 = 0, uS1 = 0, uA1 = 0, uM2 = 0, uS2 = 0, uA2 = 0;
+        if (i >= cs.lo && i < cs.hi) {
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            const T v1 = in1[r + k], v2 = in2[r + k];
+            uM1 += cs.c[0][k] * v1; uA1 += cs.c[1][k] * v1; uS1 += cs.c[2][k] * v1;
+            uM2 += cs.c[0][k] * v2; uA2 += cs.c[1][k] * v2; uS2 += cs.c[2][k] * v2;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            const T mk = BM[(size_t)k * m + i], ak = BA[(size_t)k * m + i], sk = BS[(size_t)k * m + i];
+            const T v1 = in1[r + k], v2 = in2[r + k];
+            uM1 += mk * v1; uA1 += ak * v1; uS1 += sk * v1;
+            uM2 += mk * v2; uA2 += ak * v2; uS2 += sk * v2;
+          }
+        }
+        const size_t o = (size_t)r * ld + j + P;
+        su[0 * plane + o] = a * uM1;   // -> S along x_2 for y1
+        su[1 * plane + o] = be * uS1;  // -> M along x_2 for y1
+        su[2 * plane + o] = g * uA2;   // -> A along x_2 for y1
+        su[3 * plane + o] = g * uA1;   // -> A along x_2 for y2
+        su[4 * plane + o] = a * uS2;   // -> M along x_2 for y2
+        su[5 * plane + o] = be * uM2;  // -> S along x_2 for y2
+      }
+    }
+  }
+  for (int idx = threadIdx.x; idx < 6 * TR * 2 * P; idx += blockDim.x) {
+    const int c = idx / (TR * 2 * P), rem = idx - c * TR * 2 * P;
+    const int r = rem / (2 * P), pc = rem - r * 2 * P;
+    su[c * plane + (size_t)r * ld + (pc < P ? pc : m + pc)] = T(0);
+  }
+  __syncthreads();
+  // ---- phase B: axis x_2
+  const int nc4 = (m + NC - 1) / NC;
+  double acc = 0.0;
+  for (int idx = threadIdx.x; idx < rows * nc4; idx += blockDim.x) {
+    const int r = idx / nc4, j0 = (idx - r * nc4) * NC;
+    const int i = r0 + r;
+    T s[6][NC + 2 * P];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int t = 0; t < NC + 2 * P; ++t) s[c][t] = su[c * plane + (size_t)r * ld + j0 + t];
+    const long long o1 = (long long)b * N + (long long)i * m;
+    const long long o2 = o1 + (long long)m * m;
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      const int jj = j0 + u;
+      if (jj >= m) break;
+      T y1 = 0, y2 = 0;
+      if (jj >= cs.lo && jj < cs.hi) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          y1 += cs.c[2][k] * s[0][u + k] + cs.c[0][k] * s[1][u + k] + cs.c[1][k] * s[2][u + k];
+          y2 += cs.c[1][k] * s[3][u + k] + cs.c[0][k] * s[4][u + k] + cs.c[2][k] * s[5][u + k];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const T mk = BM[(size_t)k * m + jj], ak = BA[(size_t)k * m + jj], sk = BS[(size_t)k * m + jj];
+          y1 += sk * s[0][u + k] + mk * s[1][u + k] + ak * s[2][u + k];
+          y2 += ak * s[3][u + k] + mk * s[4][u + k] + sk * s[5][u + k];
+        }
+      }
+      if (mode == 1) {
+        y1 = rhs[o1 + jj] - y1;
+        y2 = rhs[o2 + jj] - y2;
+        acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
+      } else if (dotp) {
+        acc += (double)w1[(long long)i * m + jj] * (double)y1 + (double)w2[(long long)i * m + jj] * (double)y2;
+      }
+      y[o1 + jj] = y1;
+      y[o2 + jj] = y2;
+    }
+  }
+  if (dotp) {
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0) dotp[(size_t)b * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+// ---- stencil registry: band device pointer -> central stencil of that level (host copy)
+struct StencilHost {
+  int m, P, lo, hi;
+  double c[3][13];
+};
+static std::mutex g_stencil_mu;
+static std::unordered_map<const void*, StencilHost> g_stencils;
+
+void register_level(const void* bands_dev, int m, int P, int lo, int hi, const double* central) {
+  StencilHost st{m, P, lo, hi, {}};
+  for (int x = 0; x < 3; ++x)
+    for (int k = 0; k < 2 * P + 1 && k < 13; ++k) st.c[x][k] = central[x * (2 * P + 1) + k];
+  std::lock_guard<std::mutex> lk(g_stencil_mu);
+  g_stencils[bands_dev] = st;
+}
+void unregister_level(const void* bands_dev) {
+  std::lock_guard<std::mutex> lk(g_stencil_mu);
+  g_stencils.erase(bands_dev);
+}
+static bool find_level(const void* bands_dev, StencilHost& out) {
+  std::lock_guard<std::mutex> lk(g_stencil_mu);
+  auto it = g_stencils.find(bands_dev);
+  if (it == g_stencils.end()) return false;
+  out = it->second;
+  return true;
+}
+
+template <typename T, int P, int TR>
+static void launch_v2(int m, const T* bands, const StencilHost& sh, const T* w, T* y, const T* rhs,
+                      int mode, int B, Coef c, double* dotp, int* nblk, const int* active,
+                      cudaStream_t s) {
+  Stencil<T> cs;
+  for (int x = 0; x < 3; ++x)
+    for (int k = 0; k < 13; ++k) cs.c[x][k] = k < 2 * P + 1 ? (T)sh.c[x][k] : T(0);
+  cs.lo = sh.lo;
+  cs.hi = sh.hi;
+  const size_t smem = sizeof(T) * ((size_t)6 * TR * (m + 2 * P) + 8);
+  dim3 grid((m + TR - 1) / TR, B);
+  apply2d_v2_kernel<T, P, TR><<<grid, 256, smem, s>>>(m, bands + (size_t)3 * m * (2 * P + 1), cs,
+                                                     w, y, rhs, mode, c.alpha, c.beta, active, dotp);
+  count_launch();
+  if (nblk) *nblk = grid.x;
+}
+
+template <typename T, int P>
+static bool try_v2_P(int m, const T* bands, const StencilHost& sh, const T* w, T* y, const T* rhs,
+                     int mode, int B, Coef c, double* dotp, int* nblk, const int* active,
+                     cudaStream_t s) {
+  const size_t cap = 110 * 1024;
+  auto fits = [&](int TR) { return sizeof(T) * ((size_t)6 * TR * (m + 2 * P) + 8) <= cap; };
+  if (sizeof(T) == 4 && fits(16)) {
+    launch_v2<T, P, 16>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+  } else if (sizeof(T) == 4 && fits(8)) {
+    launch_v2<T, P, 8>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+  } else if (fits(4)) {
+    launch_v2<T, P, 4>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+  } else {
+    return false;
+  }
+  return true;
+}
+
+template <typename T>
+static bool try_apply2d_v2(int m, int P, const T* bands, const T* w, T* y, const T* rhs, int mode,
+                           int B, Coef c, double* dotp, int* nblk, const int* active,
+                           cudaStream_t s) {
+  StencilHost sh;
+  if (!find_level(bands, sh) || sh.P != P) return false;
+  switch (P) {
+    case 1: return try_v2_P<T, 1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 2: return try_v2_P<T, 2>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 3: return try_v2_P<T, 3>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 4: return try_v2_P<T, 4>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 5: return try_v2_P<T, 5>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 6: return try_v2_P<T, 6>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    default: return false;
+  }
+}
+
+template <typename T, int P, int TR>
+static void set_v2_attr() {
+  cudaFuncSetAttribute(apply2d_v2_kernel<T, P, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       110 * 1024);
+}
+template <typename T, int P>
+static void set_v2_attrs() {
+  set_v2_attr<T, P, 16>();
+  set_v2_attr<T, P, 8>();
+  set_v2_attr<T, P, 4>();
 }
 
 // ------------------------------------------------------------------ generic banded axis pass
@@ -303,8 +527,14 @@ size_t apply2d_smem(int m, int P, int TR) {
 }
 
 static constexpr size_t kApplySmemCap = 200 * 1024;
+static int g_use_v2 = 1;
+void set_apply_variant(int v2) { g_use_v2 = v2; }
 
 int prepare_kernels() {
+  set_v2_attrs<float, 1>(); set_v2_attrs<float, 2>(); set_v2_attrs<float, 3>();
+  set_v2_attrs<float, 4>(); set_v2_attrs<float, 5>(); set_v2_attrs<float, 6>();
+  set_v2_attrs<double, 1>(); set_v2_attrs<double, 2>(); set_v2_attrs<double, 3>();
+  set_v2_attrs<double, 4>(); set_v2_attrs<double, 5>(); set_v2_attrs<double, 6>();
   cudaError_t e1 = cudaFuncSetAttribute(apply2d_kernel<double>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmemCap);
   cudaError_t e2 = cudaFuncSetAttribute(apply2d_kernel<float>,
@@ -317,6 +547,8 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
                  int B, Coef c, double* dotp, int* nblk, const int* active, T* scratch,
                  cudaStream_t s) {
   if (d == 2) {
+    if (g_use_v2 && try_apply2d_v2<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+      return 0;
     int TR = sizeof(T) == 8 ? 4 : 8;
     while (TR > 1 && apply2d_smem<T>(m, P, TR) > kApplySmemCap) TR /= 2;
     size_t sm = apply2d_smem<T>(m, P, TR);

@@ -4,8 +4,10 @@
 
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <string>
 #include <memory>
 #include <mutex>
 #include <tuple>
@@ -91,6 +93,10 @@ struct cd_solver_s {
   std::map<std::tuple<int, int, int, int, int, int>, std::pair<cudaGraphExec_t, uint64_t>> graphs;
   std::mutex mu;
   ~cd_solver_s() {
+    for (size_t l = 0; l < boff.size(); ++l) {
+      if (bands64.p) unregister_level(bands64.as<double>() + boff[l]);
+      if (bands32.p) unregister_level(bands32.as<float>() + boff[l]);
+    }
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
     if (h_cnt) cudaFreeHost(h_cnt);
   }
@@ -520,17 +526,58 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     A = coarsen(A);
     S = coarsen(S);
   }
+  // per level: [3][m][W] row-major bands, [3][W][m] k-major copy, padded to 4 elements
   std::vector<double> all;
+  std::vector<std::pair<int, int>> interior;
+  std::vector<std::vector<double>> central;
   for (size_t l = 0; l < h->ml.size(); ++l) {
     h->boff.push_back(all.size());
-    all.insert(all.end(), h->hM[l].v.begin(), h->hM[l].v.end());
-    all.insert(all.end(), h->hA[l].v.begin(), h->hA[l].v.end());
-    all.insert(all.end(), h->hS[l].v.begin(), h->hS[l].v.end());
+    const int ml = h->ml[l];
+    const Band* X[3] = {&h->hM[l], &h->hA[l], &h->hS[l]};
+    for (int x = 0; x < 3; ++x) all.insert(all.end(), X[x]->v.begin(), X[x]->v.end());
+    for (int x = 0; x < 3; ++x)
+      for (int k = 0; k < W; ++k)
+        for (int i = 0; i < ml; ++i) all.push_back(X[x]->v[(size_t)i * W + k]);
+    while (all.size() % 4) all.push_back(0.0);
+    // rows equal to the central row (Toeplitz part) within rounding
+    const int ic = ml / 2;
+    auto row_ok = [&](int i) {
+      for (int x = 0; x < 3; ++x) {
+        double mx = 0.0;
+        for (double v : X[x]->v) mx = std::max(mx, std::fabs(v));
+        for (int k = 0; k < W; ++k) {
+          const double a = X[x]->v[(size_t)i * W + k], c = X[x]->v[(size_t)ic * W + k];
+          if (std::fabs(a - c) > 1e-14 * mx) return false;
+        }
+      }
+      return true;
+    };
+    int lo = ic, hi = ic + 1;
+    if (ml >= 2 * W + 1) {
+      while (lo - 1 >= 0 && row_ok(lo - 1)) --lo;
+      while (hi < ml && row_ok(hi)) ++hi;
+    } else {
+      lo = hi = 0;
+    }
+    interior.push_back({lo, hi});
+    std::vector<double> c(3 * W);
+    for (int x = 0; x < 3; ++x)
+      for (int k = 0; k < W; ++k) c[x * W + k] = X[x]->v[(size_t)ic * W + k];
+    central.push_back(c);
   }
-  (void)W;
   if (upload(h->bands64, all) != cudaSuccess || upload(h->bands32, cast_vec<float>(all)) != cudaSuccess) {
     set_error("band upload failed");
     return CD_ECUDA;
+  }
+  for (size_t l = 0; l < h->ml.size(); ++l) {
+    register_level(h->bands64.as<double>() + h->boff[l], h->ml[l], P, interior[l].first,
+                   interior[l].second, central[l].data());
+    register_level(h->bands32.as<float>() + h->boff[l], h->ml[l], P, interior[l].first,
+                   interior[l].second, central[l].data());
+  }
+  {
+    const char* v = std::getenv("CURLDIV_APPLY_KERNEL");
+    set_apply_variant(v && std::string(v) == "v1" ? 0 : 1);
   }
   // FD eigenbases of the finest level
   {
