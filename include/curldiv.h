@@ -183,8 +183,28 @@ CD_API cd_status cd_restrict(cd_solver h, int level, const double* fine, double*
 CD_API cd_status cd_prolong(cd_solver h, int level, const double* coarse, double* fine,
                             int nrhs);
 
-/* Number of this library's kernels launched by the calling thread so far. */
+/* Number of this library's kernels launched by this process so far. */
 CD_API uint64_t cd_kernel_launches(void);
+
+/* y = A w for d = 3 (FP64 device vectors, layout as above, one (alpha, beta) for all
+ * nrhs right-hand sides), without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc -- code
+ * that runs inside a host framework whose allocator owns all device memory and forbids
+ * side allocations, or latency-critical paths that cannot accept the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  It computes the same product as cd_apply
+ * on a handle created for (3, p, n) with the same kernels, but needs no handle.
+ *
+ * Its working memory is a fixed 48 MiB array in the library's device image: every GPU
+ * that loads the library holds it until the process exits.  A call needs about
+ * 21 m^3 nrhs + 3 m (2p+1) + 2 nrhs doubles of it (m = n + p - 2; for one right-hand
+ * side m <= 66); larger requests return CD_EINVAL with the limit in cd_last_error().
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call
+ * shares the array and overwrites what it reads, so calls whose work overlaps on the GPU
+ * (on different streams or from different threads) race.  The call uploads the 1D bands
+ * with a small host-to-device copy and waits for that copy before launching. */
+CD_API cd_status cd_apply3d_static(int p, int n, double alpha, double beta, const double* w,
+                                   double* y, int nrhs, void* cuda_stream);
 
 #ifdef __cplusplus
 }

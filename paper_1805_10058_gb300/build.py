@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcurldiv.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["setup.cpp", "kernels.cu", "krylov.cu", "mg.cu", "solver.cu", "server.cpp"]
+SOURCES = ["setup.cpp", "kernels.cu", "krylov.cu", "mg.cu", "solver.cu", "server.cpp",
+           "static_apply.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

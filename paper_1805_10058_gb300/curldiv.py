@@ -71,6 +71,7 @@ def load(path=LIB_PATH):
         "cd_restrict": (i, [vp, i, vp, vp, i]),
         "cd_prolong": (i, [vp, i, vp, vp, i]),
         "cd_kernel_launches": (ctypes.c_uint64, []),
+        "cd_apply3d_static": (i, [i, i, d, d, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -100,6 +101,21 @@ def cd_dofs(d, p, n):
 
 def cd_kernel_launches():
     return int(load().cd_kernel_launches())
+
+
+def cd_apply3d_static(p, n, alpha, beta, w, y, stream=None, check=True):
+    """y = A w (d = 3, FP64 CUDA tensors) through the allocation-free entry point."""
+    import torch
+    lib = load()
+    N = cd_dofs(3, p, n)
+    nrhs = w.numel() // N
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = lib.cd_apply3d_static(p, n, alpha, beta, _dev(w, "float64"), _dev(y, "float64"), nrhs,
+                               ctypes.c_void_p(stream))
+    if check:
+        _check(st, "cd_apply3d_static")
+    return st
 
 
 def _params(nrhs, alphas, betas):
