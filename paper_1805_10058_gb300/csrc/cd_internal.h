@@ -70,11 +70,14 @@ int launch_apply(int d, int m, int P, const T* bands /*M,A,S*/, const T* w, T* y
 // ([3][W]: M, A, S).
 void register_level(const void* bands_dev, int m, int P, int lo, int hi, const double* central);
 void unregister_level(const void* bands_dev);
-// 1 = Toeplitz-interior kernel (default), 0 = plain shared-memory kernel (kept for checks).
-void set_apply_variant(int v2);
+// 2D apply kernel: 2 = v3 (x_2 first, packed pairs; default), 1 = v2, 0 = v1.
+void set_apply_variant(int v);
 
 // Sets kernel attributes (dynamic shared memory caps); call once before launches/captures.
 int prepare_kernels();
+
+// capacity (per solve) of the block-partial-sum arrays every reduction writes into
+constexpr int kMaxPartials = 4096;
 
 // generic reductions / vector kernels (per solve, deterministic)
 int partial_blocks(long long N);

@@ -268,6 +268,171 @@ __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
   }
 }
 
+// ------------------------------------------------------------------ 2D fused apply, v3
+// Axis x_2 first, straight from global memory: each thread computes 4 consecutive columns of
+// one input row for both components at once (packed pairs (w1, w2): one FFMA2 per tap on
+// FP32).  The results, grouped by the x_1 operator they feed,
+//   PM = (alpha S2 w1, beta S2 w2), PS = (beta M2 w1, alpha M2 w2), PA = gamma (A2 w2, A2 w1),
+// go to shared memory; then each thread owns one column and applies M1, S1, A1 along x_1 from
+// a register window, producing (y1, y2) = M1 PM + S1 PS + A1 PA with one FFMA2 per tap.
+// Tile: TR rows x 64 columns, TR + 2P rows of intermediates (halo rows recomputed).
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+__device__ __forceinline__ float2 pfma(float a, float2 x, float2 acc) {
+  return __ffma2_rn(make_float2(a, a), x, acc);
+}
+__device__ __forceinline__ double2 pfma(double a, double2 x, double2 acc) {
+  return make_double2(fma(a, x.x, acc.x), fma(a, x.y, acc.y));
+}
+template <typename T2, typename T>
+__device__ __forceinline__ T2 mk2(T a, T b) {
+  T2 r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+
+template <typename T, int P, int TR>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel(
+    int m, const T* __restrict__ bandT, Stencil<T> cs, const T* __restrict__ w,
+    T* __restrict__ y, const T* __restrict__ rhs, int mode, const double* __restrict__ alpha,
+    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp) {
+  using T2 = typename Pair<T>::type;
+  constexpr int W = 2 * P + 1;
+  constexpr int NC = 4, TC = 64, CG = TC / NC;  // 128 threads: phase A 3 rounds, phase B 1
+  constexpr int HR = TR + 2 * P;
+  constexpr int RS = TR / 2;  // rows per thread in the x_1 pass (two row segments)
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2* sp = reinterpret_cast<T2*>(smem_raw);  // [3][HR][TC]
+  const long long N = 2LL * m * m;
+  const T* w1 = w + (long long)b * N;
+  const T* w2 = w1 + (long long)m * m;
+  const int c0 = blockIdx.x * TC, r0 = blockIdx.y * TR;
+  const int rows = min(TR, m - r0), cols = min(TC, m - c0);
+  const T al = T(alpha[b]), be = T(beta[b]), ga = T(alpha[b] - beta[b]);
+  const T* BM = bandT;
+  const T* BA = bandT + (size_t)W * m;
+  const T* BS = bandT + (size_t)2 * W * m;
+  // ---- phase A: axis x_2 for rows r0-P .. r0+TR+P-1
+  for (int item = threadIdx.x; item < HR * CG; item += blockDim.x) {
+    const int q = item / CG, g = item - q * CG;
+    const int row = r0 - P + q;
+    const int j0 = c0 + g * NC;
+    T2 tM[NC], tS[NC], tA[NC];
+#pragma unroll
+    for (int u = 0; u < NC; ++u) tM[u] = tS[u] = tA[u] = mk2<T2>(T(0), T(0));
+    if (row >= 0 && row < m && j0 < m) {
+      T2 win[NC + 2 * P];
+      const T* a1 = w1 + (long long)row * m;
+      const T* a2 = w2 + (long long)row * m;
+#pragma unroll
+      for (int t = 0; t < NC + 2 * P; ++t) {
+        const int jj = j0 - P + t;
+        const bool ok = jj >= 0 && jj < m;
+        win[t] = mk2<T2>(ok ? a1[jj] : T(0), ok ? a2[jj] : T(0));
+      }
+      const bool interior = j0 >= cs.lo && j0 + NC - 1 < cs.hi;
+      if (interior) {
+#pragma unroll
+        for (int u = 0; u < NC; ++u)
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            tM[u] = pfma(cs.c[0][k], win[u + k], tM[u]);
+            tA[u] = pfma(cs.c[1][k], win[u + k], tA[u]);
+            tS[u] = pfma(cs.c[2][k], win[u + k], tS[u]);
+          }
+      } else {
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+          const int j = j0 + u;
+          if (j < m) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              tM[u] = pfma(BM[(size_t)k * m + j], win[u + k], tM[u]);
+              tA[u] = pfma(BA[(size_t)k * m + j], win[u + k], tA[u]);
+              tS[u] = pfma(BS[(size_t)k * m + j], win[u + k], tS[u]);
+            }
+          }
+        }
+      }
+    }
+    T2* pM = sp + (size_t)(0 * HR + q) * TC + g * NC;
+    T2* pS = sp + (size_t)(1 * HR + q) * TC + g * NC;
+    T2* pA = sp + (size_t)(2 * HR + q) * TC + g * NC;
+#pragma unroll
+    for (int u = 0; u < NC; ++u) {
+      pM[u] = mk2<T2>(al * tS[u].x, be * tS[u].y);  // feeds M along x_1
+      pS[u] = mk2<T2>(be * tM[u].x, al * tM[u].y);  // feeds S along x_1
+      pA[u] = mk2<T2>(ga * tA[u].y, ga * tA[u].x);  // feeds A along x_1
+    }
+  }
+  __syncthreads();
+  // ---- phase B: axis x_1, one column and RS rows per item
+  double acc = 0.0;
+  for (int item = threadIdx.x; item < 2 * TC; item += blockDim.x) {
+    const int cc = item % TC, seg = item / TC;
+    if (cc >= cols) continue;
+    const int j = c0 + cc;
+    const int rb = seg * RS;
+    if (rb >= rows) continue;
+    T2 vM[RS + 2 * P], vS[RS + 2 * P], vA[RS + 2 * P];
+#pragma unroll
+    for (int t = 0; t < RS + 2 * P; ++t) {
+      vM[t] = sp[(size_t)(0 * HR + rb + t) * TC + cc];
+      vS[t] = sp[(size_t)(1 * HR + rb + t) * TC + cc];
+      vA[t] = sp[(size_t)(2 * HR + rb + t) * TC + cc];
+    }
+#pragma unroll
+    for (int r = 0; r < RS; ++r) {
+      if (rb + r < rows) {
+        const int i = r0 + rb + r;
+        T2 yy = mk2<T2>(T(0), T(0));
+        if (i >= cs.lo && i < cs.hi) {
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            yy = pfma(cs.c[0][k], vM[r + k], yy);
+            yy = pfma(cs.c[2][k], vS[r + k], yy);
+            yy = pfma(cs.c[1][k], vA[r + k], yy);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            yy = pfma(BM[(size_t)k * m + i], vM[r + k], yy);
+            yy = pfma(BS[(size_t)k * m + i], vS[r + k], yy);
+            yy = pfma(BA[(size_t)k * m + i], vA[r + k], yy);
+          }
+        }
+        const long long o1 = (long long)b * N + (long long)i * m + j, o2 = o1 + (long long)m * m;
+        T y1 = yy.x, y2 = yy.y;
+        if (mode == 1) {
+          y1 = rhs[o1] - y1;
+          y2 = rhs[o2] - y2;
+          acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
+        } else if (dotp) {
+          acc += (double)w[o1] * (double)y1 + (double)w[o2] * (double)y2;
+        }
+        y[o1] = y1;
+        y[o2] = y2;
+      }
+    }
+  }
+  if (dotp) {
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0)
+      dotp[(size_t)b * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
 // ---- stencil registry: band device pointer -> central stencil of that level (host copy)
 struct StencilHost {
   int m, P, lo, hi;
@@ -310,6 +475,64 @@ static void launch_v2(int m, const T* bands, const StencilHost& sh, const T* w, 
                                                      w, y, rhs, mode, c.alpha, c.beta, active, dotp);
   count_launch();
   if (nblk) *nblk = grid.x;
+}
+
+template <typename T, int P, int TR>
+static void launch_v3(int m, const T* bands, const StencilHost& sh, const T* w, T* y, const T* rhs,
+                      int mode, int B, Coef c, double* dotp, int* nblk, const int* active,
+                      cudaStream_t s) {
+  Stencil<T> cs;
+  for (int x = 0; x < 3; ++x)
+    for (int k = 0; k < 13; ++k) cs.c[x][k] = k < 2 * P + 1 ? (T)sh.c[x][k] : T(0);
+  cs.lo = sh.lo;
+  cs.hi = sh.hi;
+  const size_t smem = (size_t)3 * (TR + 2 * P) * 64 * 2 * sizeof(T);
+  dim3 grid((m + 63) / 64, (m + TR - 1) / TR, B);
+  apply2d_v3_kernel<T, P, TR><<<grid, 128, smem, s>>>(m, bands + (size_t)3 * m * (2 * P + 1), cs,
+                                                     w, y, rhs, mode, c.alpha, c.beta, active, dotp);
+  count_launch();
+  if (nblk) *nblk = grid.x * grid.y;
+}
+
+template <typename T, int P>
+static bool try_v3_P(int m, const T* bands, const StencilHost& sh, const T* w, T* y, const T* rhs,
+                     int mode, int B, Coef c, double* dotp, int* nblk, const int* active,
+                     cudaStream_t s) {
+  // FP32: 16 rows per tile except P = 5 (fewest spills at 128 registers); FP64: 8 rows
+  if (sizeof(T) == 4 && P != 5)
+    launch_v3<T, P, 16>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+  else
+    launch_v3<T, P, 8>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+  return true;
+}
+
+template <typename T>
+static bool try_apply2d_v3(int m, int P, const T* bands, const T* w, T* y, const T* rhs, int mode,
+                           int B, Coef c, double* dotp, int* nblk, const int* active,
+                           cudaStream_t s) {
+  StencilHost sh;
+  if (!find_level(bands, sh) || sh.P != P) return false;
+  if ((long long)((m + 63) / 64) * ((m + 7) / 8) > kMaxPartials) return false;
+  switch (P) {
+    case 1: return try_v3_P<T, 1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 2: return try_v3_P<T, 2>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 3: return try_v3_P<T, 3>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 4: return try_v3_P<T, 4>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 5: return try_v3_P<T, 5>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 6: return try_v3_P<T, 6>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    default: return false;
+  }
+}
+
+template <typename T, int P, int TR>
+static void set_v3_attr() {
+  cudaFuncSetAttribute(apply2d_v3_kernel<T, P, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)((size_t)3 * (TR + 2 * P) * 64 * 2 * sizeof(T)));
+}
+template <typename T, int P>
+static void set_v3_attrs() {
+  set_v3_attr<T, P, 16>();
+  set_v3_attr<T, P, 8>();
 }
 
 template <typename T, int P>
@@ -527,10 +750,14 @@ size_t apply2d_smem(int m, int P, int TR) {
 }
 
 static constexpr size_t kApplySmemCap = 200 * 1024;
-static int g_use_v2 = 1;
-void set_apply_variant(int v2) { g_use_v2 = v2; }
+static int g_use_v2 = 2;  // 2: v3 kernel, 1: v2 kernel, 0: v1 kernel
+void set_apply_variant(int v) { g_use_v2 = v; }
 
 int prepare_kernels() {
+  set_v3_attrs<float, 1>(); set_v3_attrs<float, 2>(); set_v3_attrs<float, 3>();
+  set_v3_attrs<float, 4>(); set_v3_attrs<float, 5>(); set_v3_attrs<float, 6>();
+  set_v3_attrs<double, 1>(); set_v3_attrs<double, 2>(); set_v3_attrs<double, 3>();
+  set_v3_attrs<double, 4>(); set_v3_attrs<double, 5>(); set_v3_attrs<double, 6>();
   set_v2_attrs<float, 1>(); set_v2_attrs<float, 2>(); set_v2_attrs<float, 3>();
   set_v2_attrs<float, 4>(); set_v2_attrs<float, 5>(); set_v2_attrs<float, 6>();
   set_v2_attrs<double, 1>(); set_v2_attrs<double, 2>(); set_v2_attrs<double, 3>();
@@ -547,11 +774,18 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
                  int B, Coef c, double* dotp, int* nblk, const int* active, T* scratch,
                  cudaStream_t s) {
   if (d == 2) {
-    if (g_use_v2 && try_apply2d_v2<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+    // FP32: v3 (packed pairs) first; FP64: v2 first (v3's FP64 instantiation is register-bound)
+    if (g_use_v2 == 2 && sizeof(T) == 4 &&
+        try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+      return 0;
+    if (g_use_v2 >= 1 && try_apply2d_v2<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+      return 0;
+    if (g_use_v2 >= 1 && try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
       return 0;
     int TR = sizeof(T) == 8 ? 4 : 8;
     while (TR > 1 && apply2d_smem<T>(m, P, TR) > kApplySmemCap) TR /= 2;
     size_t sm = apply2d_smem<T>(m, P, TR);
+    if (sm > kApplySmemCap || (m + TR - 1) / TR > kMaxPartials) return 1;  // too large for v1
     dim3 grid((m + TR - 1) / TR, B);
     apply2d_kernel<T><<<grid, 256, sm, s>>>(m, P, TR, bands, w, y, rhs, mode, c.alpha, c.beta,
                                             active, dotp);

@@ -192,29 +192,22 @@ __device__ __forceinline__ void cheb_params(double lmax, double& theta, double& 
   delta = 0.5 * (hi - lo);
 }
 
-// d = D^{-1} r / theta; x = (xzero ? 0 : x) + d
+// d = D^{-1} r / theta; x = (xzero ? 0 : x) + d   (dinv: precomputed 1 / diag per solve)
 template <typename T>
-__global__ void __launch_bounds__(256) cheb_first_kernel(int d, int m, int P, const T* __restrict__ bands,
-                                                         const double* __restrict__ alpha,
-                                                         const double* __restrict__ beta,
+__global__ void __launch_bounds__(256) cheb_first_kernel(long long N, const T* __restrict__ dinv,
                                                          const double* __restrict__ lmax,
                                                          const T* __restrict__ r, T* __restrict__ x,
                                                          T* __restrict__ dv, int xzero,
                                                          const int* __restrict__ active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  long long nper = 1;
-  for (int l = 0; l < d; ++l) nper *= m;
-  const long long N = d * nper;
   double th, de;
   cheb_params(lmax[b], th, de);
-  const double al = alpha[b], be = beta[b];
+  const T ith = T(1.0 / th);
   const long long base = (long long)b * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
        idx += (long long)gridDim.x * blockDim.x) {
-    int comp, I[3];
-    decode(d, m, nper, idx, comp, I);
-    const T v = dinv_at<T>(d, m, P, bands, comp, I, al, be) * r[base + idx] * T(1.0 / th);
+    const T v = dinv[base + idx] * r[base + idx] * ith;
     dv[base + idx] = v;
     x[base + idx] = (xzero ? T(0) : x[base + idx]) + v;
   }
@@ -222,18 +215,13 @@ __global__ void __launch_bounds__(256) cheb_first_kernel(int d, int m, int P, co
 
 // step k >= 1: rho_k = 1/(2 sigma - rho_{k-1}); d = rho_k rho_{k-1} d + (2 rho_k / delta) D^{-1} r; x += d
 template <typename T>
-__global__ void __launch_bounds__(256) cheb_next_kernel(int d, int m, int P, const T* __restrict__ bands,
-                                                        const double* __restrict__ alpha,
-                                                        const double* __restrict__ beta,
+__global__ void __launch_bounds__(256) cheb_next_kernel(long long N, const T* __restrict__ dinv,
                                                         const double* __restrict__ lmax,
                                                         const T* __restrict__ r, T* __restrict__ x,
                                                         T* __restrict__ dv, int k,
                                                         const int* __restrict__ active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  long long nper = 1;
-  for (int l = 0; l < d; ++l) nper *= m;
-  const long long N = d * nper;
   double th, de;
   cheb_params(lmax[b], th, de);
   const double sigma = th / de;
@@ -243,15 +231,32 @@ __global__ void __launch_bounds__(256) cheb_next_kernel(int d, int m, int P, con
     rho = 1.0 / (2.0 * sigma - rho_prev);
   }
   const T c1 = T(rho * rho_prev), c2 = T(2.0 * rho / de);
-  const double al = alpha[b], be = beta[b];
+  const long long base = (long long)b * N;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const T v = c1 * dv[base + idx] + c2 * dinv[base + idx] * r[base + idx];
+    dv[base + idx] = v;
+    x[base + idx] += v;
+  }
+}
+
+// 1 / diag(A_l) for every solve, written in FP64 and FP32
+__global__ void __launch_bounds__(256) dinv_fill_kernel(int d, int m, int P, const double* __restrict__ bands,
+                                                        const double* __restrict__ alpha,
+                                                        const double* __restrict__ beta,
+                                                        double* __restrict__ d64, float* __restrict__ d32) {
+  const int b = blockIdx.y;
+  long long nper = 1;
+  for (int l = 0; l < d; ++l) nper *= m;
+  const long long N = d * nper;
   const long long base = (long long)b * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
        idx += (long long)gridDim.x * blockDim.x) {
     int comp, I[3];
     decode(d, m, nper, idx, comp, I);
-    const T v = c1 * dv[base + idx] + c2 * dinv_at<T>(d, m, P, bands, comp, I, al, be) * r[base + idx];
-    dv[base + idx] = v;
-    x[base + idx] += v;
+    const double v = dinv_at<double>(d, m, P, bands, comp, I, alpha[b], beta[b]);
+    d64[base + idx] = v;
+    d32[base + idx] = (float)v;
   }
 }
 
@@ -268,22 +273,14 @@ __global__ void hash_init_kernel(long long N, double* v, int level) {
   }
 }
 
-__global__ void __launch_bounds__(256) jacobi_scale_kernel(int d, int m, int P, const double* __restrict__ bands,
-                                                           const double* __restrict__ alpha,
-                                                           const double* __restrict__ beta,
+__global__ void __launch_bounds__(256) jacobi_scale_kernel(long long N, const double* __restrict__ dinv,
                                                            const double* __restrict__ y,
                                                            double* __restrict__ v) {
   const int b = blockIdx.y;
-  long long nper = 1;
-  for (int l = 0; l < d; ++l) nper *= m;
-  const long long N = d * nper;
   const long long base = (long long)b * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
-       idx += (long long)gridDim.x * blockDim.x) {
-    int comp, I[3];
-    decode(d, m, nper, idx, comp, I);
-    v[base + idx] = dinv_at<double>(d, m, P, bands, comp, I, alpha[b], beta[b]) * y[base + idx];
-  }
+       idx += (long long)gridDim.x * blockDim.x)
+    v[base + idx] = dinv[base + idx] * y[base + idx];
 }
 
 __global__ void norm_step_kernel(int B, const double* part, int nblk, double* lam_out,
@@ -399,14 +396,15 @@ cd_status mg_build(MgData& mg, int d, int P, const std::vector<int>& ml,
       lb.x = alloc(n * es);
       lb.r = alloc(n * es);
       lb.dv = alloc(n * es);
-      if (!lb.b || !lb.x || !lb.r || !lb.dv) return CD_ENOMEM;
+      lb.dinv = alloc(n * es);
+      if (!lb.b || !lb.x || !lb.r || !lb.dv || !lb.dinv) return CD_ENOMEM;
     }
   }
   mg.nc = (int)mg.Nl.back();
   mg.lmax = (double*)alloc(sizeof(double) * mg.L * B);
   mg.cinv64 = (double*)alloc(sizeof(double) * (size_t)B * mg.nc * mg.nc);
   mg.cinv32 = (float*)alloc(sizeof(float) * (size_t)B * mg.nc * mg.nc);
-  mg.part = (double*)alloc(sizeof(double) * (size_t)B * 1024);
+  mg.part = (double*)alloc(sizeof(double) * (size_t)B * kMaxPartials);
   mg.tmpB = (double*)alloc(sizeof(double) * B);
   // 3D scratch for levels >= 1 (the finest level uses the handle's scratch)
   if (d == 3 && mg.L > 1) {
@@ -469,11 +467,13 @@ static void mg_power(MgData& mg, int B, Coef c, double* fine_scratch64, cudaStre
     scale_kernel<<<g, 256, 0, s>>>(N, v, mg.tmpB);
     count_launch(3);
     double* scr = l == 0 ? fine_scratch64 : (double*)mg.scratch64;
+    dinv_fill_kernel<<<g, 256, 0, s>>>(mg.d, m, mg.P, level_bands<double>(mg, l), c.alpha, c.beta,
+                                       (double*)mg.lv64[l].dinv, (float*)mg.lv32[l].dinv);
+    count_launch();
     for (int it = 0; it < kPowerIts; ++it) {
       launch_apply<double>(mg.d, m, mg.P, level_bands<double>(mg, l), v, y, nullptr, 0, B, c,
                            nullptr, nullptr, nullptr, scr, s);
-      jacobi_scale_kernel<<<g, 256, 0, s>>>(mg.d, m, mg.P, level_bands<double>(mg, l), c.alpha,
-                                            c.beta, y, v);
+      jacobi_scale_kernel<<<g, 256, 0, s>>>(N, (const double*)mg.lv64[l].dinv, y, v);
       launch_dot<double>(v, v, N, B, mg.part, nb, nullptr, s);
       norm_step_kernel<<<(B + 127) / 128, 128, 0, s>>>(B, mg.part, nb, mg.lmax + (size_t)l * mg.B,
                                                        mg.tmpB);
@@ -505,14 +505,13 @@ static void smooth(MgData& mg, int l, int B, const T* bl, T* xl, bool xzero, Coe
     launch_apply<T>(mg.d, m, mg.P, bands, xl, r, bl, 1, B, c, nullptr, nullptr, active, scr, s);
     rsrc = r;
   }
-  cheb_first_kernel<T><<<g, 256, 0, s>>>(mg.d, m, mg.P, bands, c.alpha, c.beta, lm, rsrc, xl, dv,
-                                         xzero ? 1 : 0, active);
+  const T* dinv = (const T*)lb.dinv;
+  cheb_first_kernel<T><<<g, 256, 0, s>>>(N, dinv, lm, rsrc, xl, dv, xzero ? 1 : 0, active);
   count_launch();
   for (int k = 1; k < mg.deg; ++k) {
     launch_apply<T>(mg.d, m, mg.P, bands, dv, r, rsrc, 1, B, c, nullptr, nullptr, active, scr, s);
     rsrc = r;
-    cheb_next_kernel<T><<<g, 256, 0, s>>>(mg.d, m, mg.P, bands, c.alpha, c.beta, lm, r, xl, dv, k,
-                                          active);
+    cheb_next_kernel<T><<<g, 256, 0, s>>>(N, dinv, lm, r, xl, dv, k, active);
     count_launch();
   }
 }

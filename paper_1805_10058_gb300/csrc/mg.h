@@ -15,6 +15,7 @@ struct MgLevelBuf {
   void* x = nullptr;  // iterate of the level (levels >= 1)
   void* r = nullptr;  // residual
   void* dv = nullptr;  // Chebyshev direction
+  void* dinv = nullptr;  // 1 / diag(A_l) per solve, [B][N_l] (set by mg_prepare)
 };
 
 struct MgData {

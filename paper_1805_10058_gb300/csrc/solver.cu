@@ -2,6 +2,7 @@
 // preconditioners and the C-ABI entry points of include/curldiv.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -131,10 +132,11 @@ static Workspace& ws_of(cd_solver h) {
 static Coef coef_of(cd_solver h) { return Coef{h->alpha.as<double>(), h->beta.as<double>()}; }
 
 template <typename T>
-static void apply_level(cd_solver h, int level, const T* w, T* y, const T* rhs, int mode, int B,
-                        double* dotp, int* nblk, const int* active) {
-  launch_apply<T>(h->d, h->ml[level], h->P, bands_of<T>(h, level), w, y, rhs, mode, B,
-                  coef_of(h), dotp, nblk, active, ws_of<T>(h).apply_scratch.template as<T>(), h->s);
+static int apply_level(cd_solver h, int level, const T* w, T* y, const T* rhs, int mode, int B,
+                       double* dotp, int* nblk, const int* active) {
+  return launch_apply<T>(h->d, h->ml[level], h->P, bands_of<T>(h, level), w, y, rhs, mode, B,
+                         coef_of(h), dotp, nblk, active,
+                         ws_of<T>(h).apply_scratch.template as<T>(), h->s);
 }
 
 // z = B^{-1} r for the preconditioner kind pc.
@@ -393,9 +395,9 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd
     for (int g = 1; g <= 2; ++g) {
       if (cnt[g] == 0) continue;
       scale_div(N, B, h->r64.as<double>(), h->w64.r.as<double>(), h->ir_rnorm.as<double>(), m[g], h->s);
-      // the first FP64 inner solve may use the whole budget; restarts after a drifted
-      // recursive residual are capped like FP32 inner solves
-      const int cap = step == 0 ? h->opt.maxit : std::min(h->opt.maxit, h->opt.inner_maxit);
+      // the first FP64 inner solve may use the whole budget; a restart only has to correct
+      // the drift of the recursive residual (or show that the FP64 floor is reached)
+      const int cap = step == 0 ? h->opt.maxit : std::min({h->opt.maxit, h->opt.inner_maxit, 500});
       cd_status st = run_pcg<double>(h, B, pc, tol2v, cap, m[g]);
       if (st != CD_OK) return st;
       add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), m[g],
@@ -577,7 +579,7 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   }
   {
     const char* v = std::getenv("CURLDIV_APPLY_KERNEL");
-    set_apply_variant(v && std::string(v) == "v1" ? 0 : 1);
+    set_apply_variant(!v ? 2 : std::string(v) == "v1" ? 0 : std::string(v) == "v2" ? 1 : 2);
   }
   // FD eigenbases of the finest level
   {
@@ -617,7 +619,7 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   bool ok = al(h->alpha, 8 * B) && al(h->beta, 8 * B);
   for (auto& x : h->sd) ok = ok && al(x, 8 * B);
   for (auto& x : h->si) ok = ok && al(x, 4 * B);
-  for (auto& x : h->part) ok = ok && al(x, 8 * (size_t)B * 1024);
+  for (auto& x : h->part) ok = ok && al(x, 8 * (size_t)B * kMaxPartials);
   ok = ok && al(h->ir_rnorm, 8 * B) && al(h->ir_bnorm2, 8 * B) && al(h->ir_relres, 8 * B) &&
        al(h->ir_active, 4 * B) && al(h->ir_status, 4 * B) && al(h->ir_outer, 4 * B) &&
        al(h->ir_inner_total, 4 * B) && al(h->cnt, 64) && al(h->r64, 8 * (size_t)B * N) &&
@@ -676,7 +678,10 @@ cd_status cd_apply(cd_solver h, const double* w, double* y, int nrhs, const doub
   if (st != CD_OK) return st;
   std::lock_guard<std::mutex> lk(h->mu);
   if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
-  apply_level<double>(h, 0, w, y, nullptr, 0, nrhs, nullptr, nullptr, nullptr);
+  if (apply_level<double>(h, 0, w, y, nullptr, 0, nrhs, nullptr, nullptr, nullptr) != 0) {
+    set_error("no apply kernel fits this problem size");
+    return CD_EINVAL;
+  }
   CD_CUDA_OK(cudaGetLastError());
   return CD_OK;
 }
@@ -687,7 +692,10 @@ cd_status cd_apply_f32(cd_solver h, const float* w, float* y, int nrhs, const do
   if (st != CD_OK) return st;
   std::lock_guard<std::mutex> lk(h->mu);
   if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
-  apply_level<float>(h, 0, w, y, nullptr, 0, nrhs, nullptr, nullptr, nullptr);
+  if (apply_level<float>(h, 0, w, y, nullptr, 0, nrhs, nullptr, nullptr, nullptr) != 0) {
+    set_error("no apply kernel fits this problem size");
+    return CD_EINVAL;
+  }
   CD_CUDA_OK(cudaGetLastError());
   return CD_OK;
 }

@@ -35,11 +35,11 @@ APPLY_CASES = [(2, 1, 9), (2, 2, 16), (2, 3, 37), (2, 5, 30), (2, 2, 3), (2, 6, 
                (3, 1, 5), (3, 2, 7), (3, 3, 9), (3, 4, 6)]
 
 
-@pytest.mark.parametrize("variant", ["v2", "v1"])
+@pytest.mark.parametrize("variant", ["v3", "v2", "v1"])
 @pytest.mark.parametrize("d,p,n", APPLY_CASES)
 def test_apply_fp64_and_fp32_match_oracle(d, p, n, variant, monkeypatch):
-    """Both 2D kernels (Toeplitz-interior v2 and the plain shared-memory v1) against the oracle."""
-    if d == 3 and variant == "v1":
+    """Every 2D kernel (v3 default, v2, plain shared-memory v1) against the oracle."""
+    if d == 3 and variant != "v3":
         pytest.skip("one 3D kernel")
     monkeypatch.setenv("CURLDIV_APPLY_KERNEL", variant)
     alphas = np.array([1.0, 0.5, 3.0])
