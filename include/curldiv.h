@@ -186,6 +186,61 @@ CD_API cd_status cd_prolong(cd_solver h, int level, const double* coarse, double
 /* Number of this library's kernels launched by this process so far. */
 CD_API uint64_t cd_kernel_launches(void);
 
+/* ---------------------------------------------------------------- serving runtime
+ * Continuous batching of solve requests (the paper has no serving layer; this runs the
+ * solves of eq:system for many independent requests on one GPU).  Requests of one shape
+ * (d, p, n) share a cached solver; a pool of `workers` threads, each with its own CUDA
+ * stream, repeatedly takes the shape whose oldest request is oldest and solves all of its
+ * pending requests that fit in `max_batch` right-hand sides in one batched call.  Requests
+ * that arrive while their shape is on the GPU join its next batch; different shapes run
+ * concurrently.  A shape's solver is admitted when its device footprint fits in
+ * `hbm_budget`, evicting idle solvers (least recently used) when needed.  A request's
+ * results do not depend on the batch it ran in (every reduction has a fixed order per
+ * right-hand side).  Host buffers only; the server copies b at submit and x at poll/wait. */
+typedef struct cd_server_s* cd_server;
+
+typedef struct {
+  size_t hbm_budget;  /* device bytes the cached solvers may hold (0: 80% of free memory) */
+  int workers;        /* concurrent batches, one thread and stream each (default 8)        */
+  int max_batch;      /* right-hand sides per batched solve (default 16)                   */
+  double timeout_s;   /* a request still queued after this many seconds fails with
+                         CD_TIMEOUT (0: no limit)                                           */
+  cd_options solve;   /* options of every solve (default: cd_default_options, CD_PC_MG)    */
+} cd_server_options;
+
+typedef struct {
+  uint64_t submitted, completed, failed, batches, solves; /* solves = right-hand sides    */
+  double p50_s, p99_s;  /* latency (submit to completion) of completed requests           */
+  double mean_batch;    /* right-hand sides per batched call                              */
+  double solves_per_s;  /* right-hand sides solved / (last completion - first submit)     */
+  size_t bytes_in_use;  /* estimated device bytes of the cached solvers                   */
+  int handles;          /* cached solvers                                                 */
+} cd_server_stats;
+
+CD_API void cd_server_default_options(cd_server_options* opt);
+/* Starts the worker threads on the current CUDA device. */
+CD_API cd_status cd_server_create(cd_server* out, const cd_server_options* opt);
+/* Queues a request: nrhs right-hand sides (host, layout as above) with per-RHS alphas /
+ * betas (host arrays of nrhs).  CD_EINVAL for a bad shape, parameters or nrhs > max_batch. */
+CD_API cd_status cd_server_submit(cd_server s, int d, int p, int n, const double* alphas,
+                                  const double* betas, const double* b_host, int nrhs,
+                                  uint64_t* ticket);
+/* Non-blocking: *done = 0 while the request runs; when done, copies x (nrhs * cd_dofs
+ * doubles, may be NULL) and res (nrhs entries, may be NULL), releases the ticket and returns
+ * the request's worst status. */
+CD_API cd_status cd_server_poll(cd_server s, uint64_t ticket, double* x_host, cd_result* res,
+                                int* done);
+/* Blocking form of cd_server_poll (timeout_s <= 0: no limit; CD_TIMEOUT if it expires, the
+ * ticket then stays valid). */
+CD_API cd_status cd_server_wait(cd_server s, uint64_t ticket, double* x_host, cd_result* res,
+                                double timeout_s);
+/* Cancels a request that has not started (it completes with CD_CANCELLED); CD_EINVAL if it
+ * is already on the GPU or unknown. */
+CD_API cd_status cd_server_cancel(cd_server s, uint64_t ticket);
+CD_API cd_status cd_server_stats_get(cd_server s, cd_server_stats* out);
+/* Stops the workers after their current batches and frees every cached solver. */
+CD_API cd_status cd_server_destroy(cd_server s);
+
 /* y = A w for d = 3 (FP64 device vectors, layout as above, one (alpha, beta) for all
  * nrhs right-hand sides), without allocating any device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot call cudaMalloc -- code

@@ -431,6 +431,74 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd
 
 }  // namespace cd
 
+namespace cd {
+// FD eigenbases of the finest level (generalized for D, symmetric for T); built on first need.
+static cd_status ensure_fd(cd_solver h) {
+  if (h->have_fd) return CD_OK;
+  const int m = h->m, p = h->p, P = h->P;
+    std::vector<double> Md = band_to_dense(h->hM[0]), Sd = band_to_dense(h->hS[0]);
+    if (!gen_eig(m, Md, Sd, h->UD, h->lamD)) {
+      set_error("generalized eigen-decomposition failed");
+      return CD_EINVAL;
+    }
+    Band T;
+    toeplitz_T_band(p, m, P, T);
+    std::vector<double> Td = band_to_dense(T);
+    sym_eig(m, Td, h->UT, h->lamT);
+    auto transpose = [m](const std::vector<double>& U) {
+      std::vector<double> t((size_t)m * m);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) t[(size_t)j * m + i] = U[(size_t)i * m + j];
+      return t;
+    };
+    std::vector<double> UDt = transpose(h->UD), UTt = transpose(h->UT);
+    bool ok = upload(h->UD64, h->UD) == cudaSuccess && upload(h->UDt64, UDt) == cudaSuccess &&
+              upload(h->lamD64, h->lamD) == cudaSuccess && upload(h->UT64, h->UT) == cudaSuccess &&
+              upload(h->UTt64, UTt) == cudaSuccess && upload(h->lamT64, h->lamT) == cudaSuccess &&
+              upload(h->UD32, cast_vec<float>(h->UD)) == cudaSuccess &&
+              upload(h->UDt32, cast_vec<float>(UDt)) == cudaSuccess &&
+              upload(h->lamD32, cast_vec<float>(h->lamD)) == cudaSuccess &&
+              upload(h->UT32, cast_vec<float>(h->UT)) == cudaSuccess &&
+              upload(h->UTt32, cast_vec<float>(UTt)) == cudaSuccess &&
+              upload(h->lamT32, cast_vec<float>(h->lamT)) == cudaSuccess;
+    if (!ok) {
+      set_error("eigenbasis upload failed");
+      return CD_ECUDA;
+    }
+    h->have_fd = true;
+  return CD_OK;
+}
+}  // namespace cd
+
+namespace cd {
+// Device bytes a handle for (d, p, n) allocates with these options (the estimate the serving
+// runtime admits against; it mirrors the allocations of cd_create and mg_build).
+size_t solver_bytes(int d, int p, int n, const cd_options& opt) {
+  const size_t B = (size_t)std::max(1, opt.max_batch);
+  const size_t N = cd_dofs(d, p, n);
+  const int m = n + p - 2, W = 2 * p + 1;
+  size_t bytes = 0;
+  size_t nl = 0, n3 = 0, n3_1 = 0;
+  for (int ml = m, l = 0;; ++l) {
+    nl += 2 * (size_t)3 * ml * W + 8;  // bands of the level
+    if (l == 0) n3 = (size_t)ml * ml * ml;
+    if (l == 1) n3_1 = (size_t)ml * ml * ml;
+    if (ml <= std::max(1, opt.mg_m_min) || ml / 2 < 1) break;
+    ml /= 2;
+  }
+  bytes += nl * 12;
+  bytes += B * N * (7 * 8 + 7 * 4 + 8 + 16);  // Krylov workspaces, r64, b64/x64
+  if (d == 3) bytes += 21 * n3 * B * 12;
+  bytes += 4 * 8 * B * kMaxPartials + 64 * B;
+  // multigrid levels: five vectors per level and precision (level sizes shrink by 2^d)
+  bytes += (size_t)(5 * 12 * (double)B * N * (d == 2 ? 4.0 / 3.0 : 8.0 / 7.0));
+  if (d == 3) bytes += 21 * n3_1 * B * 12;
+  if (opt.precond == CD_PC_FD_D || opt.precond == CD_PC_FD_T)
+    bytes += (size_t)m * m * 12 * 4;
+  return (size_t)(1.1 * (double)bytes) + (64u << 20);
+}
+}  // namespace cd
+
 // ====================================================================== C ABI
 extern "C" {
 
@@ -581,38 +649,9 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     const char* v = std::getenv("CURLDIV_APPLY_KERNEL");
     set_apply_variant(!v ? 2 : std::string(v) == "v1" ? 0 : std::string(v) == "v2" ? 1 : 2);
   }
-  // FD eigenbases of the finest level
-  {
-    std::vector<double> Md = band_to_dense(h->hM[0]), Sd = band_to_dense(h->hS[0]);
-    if (!gen_eig(m, Md, Sd, h->UD, h->lamD)) {
-      set_error("generalized eigen-decomposition failed");
-      return CD_EINVAL;
-    }
-    Band T;
-    toeplitz_T_band(p, m, P, T);
-    std::vector<double> Td = band_to_dense(T);
-    sym_eig(m, Td, h->UT, h->lamT);
-    auto transpose = [m](const std::vector<double>& U) {
-      std::vector<double> t((size_t)m * m);
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < m; ++j) t[(size_t)j * m + i] = U[(size_t)i * m + j];
-      return t;
-    };
-    std::vector<double> UDt = transpose(h->UD), UTt = transpose(h->UT);
-    bool ok = upload(h->UD64, h->UD) == cudaSuccess && upload(h->UDt64, UDt) == cudaSuccess &&
-              upload(h->lamD64, h->lamD) == cudaSuccess && upload(h->UT64, h->UT) == cudaSuccess &&
-              upload(h->UTt64, UTt) == cudaSuccess && upload(h->lamT64, h->lamT) == cudaSuccess &&
-              upload(h->UD32, cast_vec<float>(h->UD)) == cudaSuccess &&
-              upload(h->UDt32, cast_vec<float>(UDt)) == cudaSuccess &&
-              upload(h->lamD32, cast_vec<float>(h->lamD)) == cudaSuccess &&
-              upload(h->UT32, cast_vec<float>(h->UT)) == cudaSuccess &&
-              upload(h->UTt32, cast_vec<float>(UTt)) == cudaSuccess &&
-              upload(h->lamT32, cast_vec<float>(h->lamT)) == cudaSuccess;
-    if (!ok) {
-      set_error("eigenbasis upload failed");
-      return CD_ECUDA;
-    }
-    h->have_fd = true;
+  if (h->opt.precond == CD_PC_FD_D || h->opt.precond == CD_PC_FD_T) {
+    cd_status st = ensure_fd(h.get());
+    if (st != CD_OK) return st;
   }
   // workspace
   auto al = [&](DevBuf& bfr, size_t bytes) { return bfr.alloc(bytes) == cudaSuccess; };
@@ -737,6 +776,10 @@ cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs, co
   if (st != CD_OK) return st;
   if (kind < CD_PC_NONE || kind > CD_PC_MG) return CD_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
+  if (kind == CD_PC_FD_D || kind == CD_PC_FD_T) {
+    st = ensure_fd(h);
+    if (st != CD_OK) return st;
+  }
   st = set_params(h, nrhs, alphas, betas, nullptr, nullptr, kind == CD_PC_MG);
   if (st != CD_OK) return st;
   if (f32)
@@ -762,7 +805,12 @@ cd_status cd_get_bands(cd_solver h, int level, double* M, double* A, double* S, 
 }
 
 cd_status cd_get_eig(cd_solver h, int which, double* U, double* lam) {
-  if (!h || !h->have_fd || (which != 0 && which != 1)) return CD_EINVAL;
+  if (!h || (which != 0 && which != 1)) return CD_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(h->mu);
+    cd_status st = ensure_fd(h);
+    if (st != CD_OK) return st;
+  }
   const std::vector<double>& Us = which == 0 ? h->UD : h->UT;
   const std::vector<double>& ls = which == 0 ? h->lamD : h->lamT;
   if (U) std::memcpy(U, Us.data(), Us.size() * 8);

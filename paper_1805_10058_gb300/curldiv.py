@@ -35,6 +35,21 @@ class Result(ctypes.Structure):
                     relres=self.relres, seconds=self.seconds, status=self.status)
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("timeout_s", ctypes.c_double), ("solve", Options)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("solves", ctypes.c_uint64), ("p50_s", ctypes.c_double),
+                ("p99_s", ctypes.c_double), ("mean_batch", ctypes.c_double), ("solves_per_s", ctypes.c_double),
+                ("bytes_in_use", ctypes.c_size_t), ("handles", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class CurlDivError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{msg} (status {status})")
@@ -72,6 +87,14 @@ def load(path=LIB_PATH):
         "cd_prolong": (i, [vp, i, vp, vp, i]),
         "cd_kernel_launches": (ctypes.c_uint64, []),
         "cd_apply3d_static": (i, [i, i, d, d, vp, vp, i, vp]),
+        "cd_server_default_options": (None, [ctypes.POINTER(ServerOptions)]),
+        "cd_server_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(ServerOptions)]),
+        "cd_server_submit": (i, [vp, i, i, i, dp, dp, dp, i, ctypes.POINTER(ctypes.c_uint64)]),
+        "cd_server_poll": (i, [vp, ctypes.c_uint64, dp, ctypes.POINTER(Result), ctypes.POINTER(i)]),
+        "cd_server_wait": (i, [vp, ctypes.c_uint64, dp, ctypes.POINTER(Result), d]),
+        "cd_server_cancel": (i, [vp, ctypes.c_uint64]),
+        "cd_server_stats_get": (i, [vp, ctypes.POINTER(ServerStats)]),
+        "cd_server_destroy": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -240,3 +263,82 @@ class Solver:
         for _ in range(level):
             m //= 2
         return m
+
+
+def server_options(**kw):
+    o = ServerOptions()
+    load().cd_server_default_options(ctypes.byref(o))
+    solve = kw.pop("solve", {})
+    for k, v in kw.items():
+        setattr(o, k, v)
+    for k, v in solve.items():
+        setattr(o.solve, k, v)
+    return o
+
+
+class Server:
+    """Continuous-batching solve server (cd_server_*); host numpy buffers."""
+
+    def __init__(self, **kw):
+        self.lib = load()
+        self.opts = server_options(**kw)
+        h = ctypes.c_void_p()
+        _check(self.lib.cd_server_create(ctypes.byref(h), ctypes.byref(self.opts)), "cd_server_create")
+        self.h = h
+        self.meta = {}
+
+    def submit(self, d, p, n, alphas, betas, b):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        N = cd_dofs(d, p, n)
+        nrhs = b.size // N
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(alphas, dtype=np.float64), (nrhs,)))
+        be = np.ascontiguousarray(np.broadcast_to(np.asarray(betas, dtype=np.float64), (nrhs,)))
+        t = ctypes.c_uint64()
+        P = ctypes.POINTER(ctypes.c_double)
+        st = self.lib.cd_server_submit(self.h, d, p, n, a.ctypes.data_as(P), be.ctypes.data_as(P),
+                                       b.ctypes.data_as(P), nrhs, ctypes.byref(t))
+        _check(st, "cd_server_submit")
+        self.meta[t.value] = (N, nrhs)
+        return t.value
+
+    def _out(self, ticket):
+        N, nrhs = self.meta[ticket]
+        return np.zeros(N * nrhs), (Result * nrhs)()
+
+    def poll(self, ticket):
+        x, res = self._out(ticket)
+        done = ctypes.c_int()
+        st = self.lib.cd_server_poll(self.h, ticket, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     res, ctypes.byref(done))
+        if not done.value:
+            return None
+        self.meta.pop(ticket)
+        return st, x, [r.as_dict() for r in res]
+
+    def wait(self, ticket, timeout_s=0.0):
+        x, res = self._out(ticket)
+        st = self.lib.cd_server_wait(self.h, ticket, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     res, timeout_s)
+        if st == CD_TIMEOUT and timeout_s > 0:
+            return None
+        self.meta.pop(ticket, None)
+        return st, x, [r.as_dict() for r in res]
+
+    def cancel(self, ticket):
+        return self.lib.cd_server_cancel(self.h, ticket)
+
+    def stats(self):
+        s = ServerStats()
+        _check(self.lib.cd_server_stats_get(self.h, ctypes.byref(s)), "cd_server_stats_get")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
