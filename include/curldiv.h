@@ -99,7 +99,9 @@ typedef struct {
   int chunk;          /* iterations per graph launch / host convergence poll (8)  */
   double mixed_switch_ratio; /* FP32-IR: parameter ratio above which the inner
                                 Krylov solve is FP64 (default 1e4)                 */
-  int reserved[8];
+  int fd_tensor_cores; /* FP32 FD transforms on tcgen05 (TF32 operands, FP32
+                          accumulation; the Krylov method is then flexible) (1)   */
+  int reserved[7];
 } cd_options;
 
 typedef struct {

@@ -35,6 +35,12 @@ template <typename T>
 int launch_fd_axis(int d, int m, int axis, int B, const T* G, const T* in, T* out,
                    FdScale<T> sc, const int* active, cudaStream_t s);
 
+// tcgen05 (TF32) version of launch_fd_axis<float>; fd_tc_error() reports a bounded wait that
+// expired inside the kernel (then its output is not written).
+bool launch_fd_axis_tc(int d, int m, int axis, int B, const float* G, const float* in, float* out,
+                       FdScale<float> sc, cudaStream_t s);
+int fd_tc_error();
+
 template <typename T>
 void vcopy(long long N, int B, const T* src, T* dst, const int* active, cudaStream_t s);
 template <typename T>

@@ -139,6 +139,17 @@ static int apply_level(cd_solver h, int level, const T* w, T* y, const T* rhs, i
                          ws_of<T>(h).apply_scratch.template as<T>(), h->s);
 }
 
+// One FD pass: FP32 on tcgen05 when enabled (all solves of the batch), else SIMT.
+template <typename T>
+static void fd_pass(cd_solver h, int axis, int B, const T* G, const T* in, T* out, FdScale<T> sc,
+                    const int* active) {
+  if (sizeof(T) == 4 && h->opt.fd_tensor_cores &&
+      launch_fd_axis_tc(h->d, h->m, axis, B, (const float*)G, (const float*)in, (float*)out,
+                        *reinterpret_cast<FdScale<float>*>(&sc), h->s))
+    return;
+  launch_fd_axis<T>(h->d, h->m, axis, B, G, in, out, sc, active, h->s);
+}
+
 // z = B^{-1} r for the preconditioner kind pc.
 template <typename T>
 static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* active) {
@@ -179,13 +190,13 @@ static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* 
       sc.beta = h->beta.as<double>();
       sc.base = dst;
     }
-    launch_fd_axis<T>(d, m, a, B, U, src, dst, sc, active, h->s);
+    fd_pass<T>(h, a, B, U, src, dst, sc, active);
     src = dst;
     ++pass;
   }
   for (int a = d - 1; a >= 0; --a) {  // backward: U along every axis
     T* dst = (a == 0) ? z : bufs[pass & 1];
-    launch_fd_axis<T>(d, m, a, B, Ut, src, dst, FdScale<T>{}, active, h->s);
+    fd_pass<T>(h, a, B, Ut, src, dst, FdScale<T>{}, active);
     src = dst;
     ++pass;
   }
@@ -222,7 +233,10 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
   PcgState st = state_of(h);
   const long long N = h->N;
   const int nb = partial_blocks(N);
-  const int flexible = (pc == CD_PC_MG) ? 1 : 0;
+  // a Krylov-smoothed / multigrid or tensor-core (TF32) preconditioner is not an exactly
+  // fixed symmetric operator: use the flexible update there
+  const int flexible =
+      (pc == CD_PC_MG || (sizeof(T) == 4 && h->opt.fd_tensor_cores && pc != CD_PC_NONE)) ? 1 : 0;
   vzero<T>(N, B, w.x.as<T>(), outer_active, h->s);
   apply_prec<T>(h, pc, B, w.r.as<T>(), w.z.as<T>(), outer_active);
   launch_dot<T>(w.r.as<T>(), w.r.as<T>(), N, B, h->part[1].as<double>(), nb, outer_active, h->s);
@@ -409,6 +423,11 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd
   CD_CUDA_OK(cudaMemcpyAsync(status.data(), h->ir_status.p, B * 4, cudaMemcpyDeviceToHost, h->s));
   CD_CUDA_OK(cudaMemcpyAsync(inner.data(), h->ir_inner_total.p, B * 4, cudaMemcpyDeviceToHost, h->s));
   CD_CUDA_OK(cudaMemcpyAsync(outer.data(), h->ir_outer.p, B * 4, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaStreamSynchronize(h->s));
+  if (fd_tc_error()) {
+    set_error("a tensor-core FD kernel gave up waiting for its MMAs");
+    return CD_ECUDA;
+  }
   std::vector<double> rel;
   cd_status st = final_residual(h, B, b, x, rel);
   if (st != CD_OK) return st;
@@ -518,6 +537,7 @@ void cd_default_options(cd_options* o) {
   o->use_graphs = 1;
   o->chunk = 8;
   o->mixed_switch_ratio = 1e4;
+  o->fd_tensor_cores = 1;
 }
 
 size_t cd_dofs(int d, int p, int n) {

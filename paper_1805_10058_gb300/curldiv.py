@@ -23,7 +23,8 @@ class Options(ctypes.Structure):
                 ("inner_rtol", ctypes.c_double), ("inner_maxit", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("mg_m_min", ctypes.c_int), ("use_graphs", ctypes.c_int), ("chunk", ctypes.c_int),
-                ("mixed_switch_ratio", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+                ("mixed_switch_ratio", ctypes.c_double), ("fd_tensor_cores", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class Result(ctypes.Structure):

@@ -120,12 +120,18 @@ def test_fd_preconditioners_match_direct_solves(d, p, n):
     Z = host(z).reshape(2, -1)
     z32 = torch.zeros(2 * s.N, dtype=torch.float32, device="cuda")
     s.cd_precond(cdl.CD_PC_FD_D, dev(R.ravel(), torch.float32), z32, alphas, betas)
-    Z32 = host(z32).reshape(2, -1)
+    Z32 = host(z32).reshape(2, -1)  # tcgen05, TF32 operands
+    s_simt = cdl.Solver(d, p, n, max_batch=2, fd_tensor_cores=0)
+    z32s = torch.zeros(2 * s.N, dtype=torch.float32, device="cuda")
+    s_simt.cd_precond(cdl.CD_PC_FD_D, dev(R.ravel(), torch.float32), z32s, alphas, betas)
+    Z32s = host(z32s).reshape(2, -1)  # SIMT FP32
     for k in range(2):
         A = oracle_matrix(d, p, n, alphas[k], betas[k])
         ref = solvers.solve_D(A, d, R[k])
         assert np.linalg.norm(Z[k] - ref) <= 1e-10 * np.linalg.norm(ref)
-        assert np.linalg.norm(Z32[k] - ref) <= 1e-4 * np.linalg.norm(ref)
+        assert np.linalg.norm(Z32s[k] - ref) <= 1e-4 * np.linalg.norm(ref)
+        # TF32 keeps 10 mantissa bits (unit roundoff 2^-11 ~ 4.9e-4) through four passes
+        assert np.linalg.norm(Z32[k] - ref) <= 5e-3 * np.linalg.norm(ref)
     zt = torch.zeros(2 * s.N, dtype=torch.float64, device="cuda")
     s.cd_precond(cdl.CD_PC_FD_T, dev(R.ravel()), zt, alphas, betas)
     ZT = host(zt).reshape(2, -1)
