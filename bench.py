@@ -33,6 +33,7 @@ N_INT = 256
 BETAS = (1e-6, 1e-3, 1.0, 1e3, 1e6)
 SEEDS = tuple(range(8))
 RTOL = 1e-10
+APPLY_KERNEL_TAG = "apply2d_v3_t64"  # FP32 2D apply variant whose ncu counters are committed
 WORKLOAD = ("2D curl-div sweep: p in {2,3,4}, n=256 (~131k-133k DoF/solve), alpha=1, "
             "beta in {1e-6,1e-3,1,1e3,1e6}, 8 uniform[-1,1] RHS per case (120 solves), "
             "MG-preconditioned FCG, FP32 inner + FP64 refinement, rtol 1e-10")
@@ -284,14 +285,18 @@ def run_ours(args):
     t_apply = statistics.mean(times) / 1e3
     alg_bytes = 2 * B * s.N * 4
     achieved = alg_bytes / t_apply / 1e9
+    # DRAM bytes of one launch from the committed ncu summary, only if it was taken on the
+    # kernel version that runs now
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", "apply_traffic.json")) as f:
-            tr = json.load(f)
-        if tr.get("kernel_version") == "apply2d_v1":
-            traffic = tr.get("bytes_per_launch")
+        with open(os.path.join(ROOT, "profiles", "apply2d_v3_fp32_p3_n256_b40.md")) as f:
+            for line in f:
+                if line.startswith("roofline-traffic-per-launch:"):
+                    val, tag = line.split(":", 1)[1].split("(kernel")
+                    if tag.strip(" )\n") == APPLY_KERNEL_TAG:
+                        traffic = int(val.strip())
     except Exception:
-        pass
+        traffic = None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -311,7 +316,7 @@ def run_ours(args):
                         "d2h_bytes_per_step": h2d},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": "apply2d_kernel<float> (p=3, n=256, batch 40)",
+                             "kernel": "apply2d_v3_kernel<float> (p=3, n=256, batch 40)",
                              "launch_us": t_apply * 1e6},
                 "gpu_launches": int(launches),
                 "clocks": clk}
