@@ -33,7 +33,7 @@ N_INT = 256
 BETAS = (1e-6, 1e-3, 1.0, 1e3, 1e6)
 SEEDS = tuple(range(8))
 RTOL = 1e-10
-APPLY_KERNEL_TAG = "apply2d_v3_t64"  # FP32 2D apply variant whose ncu counters are committed
+APPLY_KERNEL_TAG = "apply2d_v3_t64_epi"  # FP32 2D apply version; traffic is read only if the committed ncu counters are for it
 WORKLOAD = ("2D curl-div sweep: p in {2,3,4}, n=256 (~131k-133k DoF/solve), alpha=1, "
             "beta in {1e-6,1e-3,1,1e3,1e6}, 8 uniform[-1,1] RHS per case (120 solves), "
             "MG-preconditioned FCG, FP32 inner + FP64 refinement, rtol 1e-10")

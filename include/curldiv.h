@@ -101,7 +101,10 @@ typedef struct {
                                 Krylov solve is FP64 (default 1e4)                 */
   int fd_tensor_cores; /* FP32 FD transforms on tcgen05 (TF32 operands, FP32
                           accumulation; the Krylov method is then flexible) (1)   */
-  int reserved[7];
+  int autotune;        /* time the tilings of the FP32 2D apply for this shape at
+                          cd_create and keep the fastest; tilings give identical
+                          results, so the choice never changes a solve (1)        */
+  int reserved[6];
 } cd_options;
 
 typedef struct {

@@ -58,12 +58,31 @@ struct Coef {  // per-solve operator coefficients, device arrays of length >= B
   const double* beta;
 };
 
+// Chebyshev smoother interval on D^{-1} A: [kChebHi lambda_max / kChebRatio, kChebHi lambda_max]
+constexpr double kChebHi = 1.1, kChebRatio = 30.0;
+
+// Epilogue of mode 2 (a Chebyshev smoothing step fused into the apply): with r = rhs - A w at
+// each output point and 1/diag(A) computed from the 1D band diagonals,
+//   d = (step == 0) ? r / (theta diag) : c1 dprev + c2 r / diag,   xout = xprev + d,
+// optionally dout = d and rout = r.  Nothing is written to y.  (dprev, xprev are read only at
+// the output point; w is read with halos, so w must not alias xout, dout or rout.)
+template <typename T>
+struct Epi {
+  const T* dprev;
+  const T* xprev;
+  T* xout;
+  T* dout;
+  T* rout;
+  const double* lmax;  // per solve: largest eigenvalue estimate of D^{-1} A
+  int step;
+};
+
 // y = A w (mode 0) or y = b - A w (mode 1) on one level; optional per-solve partial dots
 // dotp[b * nblk + blk] = sum over the block of w * y (mode 0) or y * y (mode 1).
 template <typename T>
 int launch_apply(int d, int m, int P, const T* bands /*M,A,S*/, const T* w, T* y,
                  const T* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
-                 const int* active, T* scratch, cudaStream_t s);
+                 const int* active, T* scratch, cudaStream_t s, const Epi<T>* epi = nullptr);
 
 // Central-stencil registry for the 2D apply: `bands_dev` is the start of a level's band
 // block ([3][m][W] row-major, then [3][W][m] k-major); rows [lo, hi) equal `central`
@@ -72,6 +91,14 @@ void register_level(const void* bands_dev, int m, int P, int lo, int hi, const d
 void unregister_level(const void* bands_dev);
 // 2D apply kernel: 2 = v3 (x_2 first, packed pairs; default), 1 = v2, 0 = v1.
 void set_apply_variant(int v);
+
+// Autotuner of the 2D apply: times the variants on (m, P, B) and records the fastest
+// (returns the chosen variant, 0 if none was tuned).  Not inside a stream capture.
+template <typename T>
+int tune_apply2d(int m, int P, const T* bands, const T* w, T* y, int B, Coef c, cudaStream_t s);
+
+template <typename T>
+bool apply_can_fuse(int d, int m, int P, const T* bands, int B);
 
 // Sets kernel attributes (dynamic shared memory caps); call once before launches/captures.
 int prepare_kernels();

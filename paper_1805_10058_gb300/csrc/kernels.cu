@@ -16,7 +16,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <unordered_map>
 
 #include "cd_internal.h"
@@ -43,6 +45,33 @@ __device__ double block_sum(double v) {
     s = warp_sum(s);
   }
   return s;
+}
+
+// Chebyshev step coefficients of one solve: d = c1 dprev + c2 D^{-1} r (c1 = 0 for step 0).
+__device__ __forceinline__ void cheb_coef(double lmax, int step, double& c1, double& c2) {
+  const double hi = kChebHi * lmax, lo = hi / kChebRatio;
+  const double th = 0.5 * (hi + lo), de = 0.5 * (hi - lo), sigma = th / de;
+  if (step == 0) {
+    c1 = 0.0;
+    c2 = 1.0 / th;
+    return;
+  }
+  double rho_prev = 1.0 / sigma, rho = rho_prev;
+  for (int j = 1; j <= step; ++j) {
+    rho_prev = rho;
+    rho = 1.0 / (2.0 * sigma - rho_prev);
+  }
+  c1 = rho * rho_prev;
+  c2 = 2.0 * rho / de;
+}
+
+template <typename T>
+__device__ __forceinline__ void cheb_epi(const Epi<T>& e, long long o, T r, T dinv, T c1, T c2) {
+  T d = c2 * dinv * r;
+  if (e.step > 0) d += c1 * e.dprev[o];
+  e.xout[o] = e.xprev[o] + d;
+  if (e.dout) e.dout[o] = d;
+  if (e.rout) e.rout[o] = r;
 }
 
 // ------------------------------------------------------------------ 2D fused apply
@@ -154,7 +183,8 @@ template <typename T, int P, int TR>
 __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
     int m, const T* __restrict__ bandT, Stencil<T> cs, const T* __restrict__ w,
     T* __restrict__ y, const T* __restrict__ rhs, int mode, const double* __restrict__ alpha,
-    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp) {
+    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp,
+    Epi<T> epi) {
   constexpr int W = 2 * P + 1;
   constexpr int NC = sizeof(T) == 8 ? 2 : 4;  // outputs per thread along x_2
   const int b = blockIdx.y;
@@ -222,6 +252,13 @@ __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
   // ---- phase B: axis x_2
   const int nc4 = (m + NC - 1) / NC;
   double acc = 0.0;
+  T ec1 = 0, ec2 = 0;
+  if (mode == 2) {
+    double c1, c2;
+    cheb_coef(epi.lmax[b], epi.step, c1, c2);
+    ec1 = T(c1);
+    ec2 = T(c2);
+  }
   for (int idx = threadIdx.x; idx < rows * nc4; idx += blockDim.x) {
     const int r = idx / nc4, j0 = (idx - r * nc4) * NC;
     const int i = r0 + r;
@@ -250,6 +287,13 @@ __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
           y1 += sk * s[0][u + k] + mk * s[1][u + k] + ak * s[2][u + k];
           y2 += ak * s[3][u + k] + mk * s[4][u + k] + sk * s[5][u + k];
         }
+      }
+      if (mode == 2) {
+        const T Mi = BM[(size_t)P * m + i], Si = BS[(size_t)P * m + i];
+        const T Mj = BM[(size_t)P * m + jj], Sj = BS[(size_t)P * m + jj];
+        cheb_epi(epi, o1 + jj, rhs[o1 + jj] - y1, T(1) / (be * Si * Mj + a * Mi * Sj), ec1, ec2);
+        cheb_epi(epi, o2 + jj, rhs[o2 + jj] - y2, T(1) / (a * Si * Mj + be * Mi * Sj), ec1, ec2);
+        continue;
       }
       if (mode == 1) {
         y1 = rhs[o1 + jj] - y1;
@@ -304,7 +348,8 @@ template <typename T, int P, int TR>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel(
     int m, const T* __restrict__ bandT, Stencil<T> cs, const T* __restrict__ w,
     T* __restrict__ y, const T* __restrict__ rhs, int mode, const double* __restrict__ alpha,
-    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp) {
+    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp,
+    Epi<T> epi) {
   using T2 = typename Pair<T>::type;
   constexpr int W = 2 * P + 1;
   constexpr int NC = 4, TC = 64, CG = TC / NC;  // 128 threads: phase A 3 rounds, phase B 1
@@ -379,6 +424,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel
   __syncthreads();
   // ---- phase B: axis x_1, one column and RS rows per item
   double acc = 0.0;
+  T ec1 = 0, ec2 = 0;
+  if (mode == 2) {
+    double c1, c2;
+    cheb_coef(epi.lmax[b], epi.step, c1, c2);
+    ec1 = T(c1);
+    ec2 = T(c2);
+  }
   for (int item = threadIdx.x; item < 2 * TC; item += blockDim.x) {
     const int cc = item % TC, seg = item / TC;
     if (cc >= cols) continue;
@@ -414,6 +466,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel
         }
         const long long o1 = (long long)b * N + (long long)i * m + j, o2 = o1 + (long long)m * m;
         T y1 = yy.x, y2 = yy.y;
+        if (mode == 2) {
+          const T Mi = BM[(size_t)P * m + i], Si = BS[(size_t)P * m + i];
+          const T Mj = BM[(size_t)P * m + j], Sj = BS[(size_t)P * m + j];
+          cheb_epi(epi, o1, rhs[o1] - y1, T(1) / (be * Si * Mj + al * Mi * Sj), ec1, ec2);
+          cheb_epi(epi, o2, rhs[o2] - y2, T(1) / (al * Si * Mj + be * Mi * Sj), ec1, ec2);
+          continue;
+        }
         if (mode == 1) {
           y1 = rhs[o1] - y1;
           y2 = rhs[o2] - y2;
@@ -460,6 +519,9 @@ static bool find_level(const void* bands_dev, StencilHost& out) {
   return true;
 }
 
+template <typename T>
+static thread_local Epi<T> g_epi{};  // epilogue of the launch in progress (mode 2)
+
 template <typename T, int P, int TR>
 static void launch_v2(int m, const T* bands, const StencilHost& sh, const T* w, T* y, const T* rhs,
                       int mode, int B, Coef c, double* dotp, int* nblk, const int* active,
@@ -472,7 +534,8 @@ static void launch_v2(int m, const T* bands, const StencilHost& sh, const T* w, 
   const size_t smem = sizeof(T) * ((size_t)6 * TR * (m + 2 * P) + 8);
   dim3 grid((m + TR - 1) / TR, B);
   apply2d_v2_kernel<T, P, TR><<<grid, 256, smem, s>>>(m, bands + (size_t)3 * m * (2 * P + 1), cs,
-                                                     w, y, rhs, mode, c.alpha, c.beta, active, dotp);
+                                                     w, y, rhs, mode, c.alpha, c.beta, active, dotp,
+                                                     g_epi<T>);
   count_launch();
   if (nblk) *nblk = grid.x;
 }
@@ -489,9 +552,21 @@ static void launch_v3(int m, const T* bands, const StencilHost& sh, const T* w, 
   const size_t smem = (size_t)3 * (TR + 2 * P) * 64 * 2 * sizeof(T);
   dim3 grid((m + 63) / 64, (m + TR - 1) / TR, B);
   apply2d_v3_kernel<T, P, TR><<<grid, 128, smem, s>>>(m, bands + (size_t)3 * m * (2 * P + 1), cs,
-                                                     w, y, rhs, mode, c.alpha, c.beta, active, dotp);
+                                                     w, y, rhs, mode, c.alpha, c.beta, active, dotp,
+                                                     g_epi<T>);
   count_launch();
   if (nblk) *nblk = grid.x * grid.y;
+}
+
+template <typename T, int P>
+static bool try_v3_P_tr(int TR, int m, const T* bands, const StencilHost& sh, const T* w, T* y,
+                        const T* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                        const int* active, cudaStream_t s) {
+  if (TR == 16)
+    launch_v3<T, P, 16>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+  else
+    launch_v3<T, P, 8>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+  return true;
 }
 
 template <typename T, int P>
@@ -509,10 +584,21 @@ static bool try_v3_P(int m, const T* bands, const StencilHost& sh, const T* w, T
 template <typename T>
 static bool try_apply2d_v3(int m, int P, const T* bands, const T* w, T* y, const T* rhs, int mode,
                            int B, Coef c, double* dotp, int* nblk, const int* active,
-                           cudaStream_t s) {
+                           cudaStream_t s, int TR = 0) {
   StencilHost sh;
   if (!find_level(bands, sh) || sh.P != P) return false;
   if ((long long)((m + 63) / 64) * ((m + 7) / 8) > kMaxPartials) return false;
+  if (TR == 8 || TR == 16) {
+    switch (P) {
+      case 1: return try_v3_P_tr<T, 1>(TR, m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+      case 2: return try_v3_P_tr<T, 2>(TR, m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+      case 3: return try_v3_P_tr<T, 3>(TR, m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+      case 4: return try_v3_P_tr<T, 4>(TR, m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+      case 5: return try_v3_P_tr<T, 5>(TR, m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+      case 6: return try_v3_P_tr<T, 6>(TR, m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+      default: return false;
+    }
+  }
   switch (P) {
     case 1: return try_v3_P<T, 1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
     case 2: return try_v3_P<T, 2>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
@@ -716,15 +802,42 @@ template <typename T>
 __global__ void __launch_bounds__(256) post3d_kernel(long long N, const T* __restrict__ w,
                                                      const T* ytmp, T* y, const T* rhs,
                                                      int mode, const int* __restrict__ active,
-                                                     double* __restrict__ dotp) {
+                                                     double* __restrict__ dotp, int m, int P,
+                                                     const T* __restrict__ bands,
+                                                     const double* __restrict__ alpha,
+                                                     const double* __restrict__ beta, Epi<T> epi) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const long long chunk = (N + gridDim.x - 1) / gridDim.x;
   const long long lo = (long long)blockIdx.x * chunk, hi = min(N, lo + chunk);
   const long long base = (long long)b * N;
   double acc = 0.0;
+  T ec1 = 0, ec2 = 0;
+  if (mode == 2) {
+    double c1, c2;
+    cheb_coef(epi.lmax[b], epi.step, c1, c2);
+    ec1 = T(c1);
+    ec2 = T(c2);
+  }
+  const int W = 2 * P + 1;
+  const long long n3 = N / 3;
   for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
     T v = ytmp[base + i];
+    if (mode == 2) {
+      const int comp = (int)(i / n3);
+      long long rem = i - comp * n3;
+      const int i2 = (int)(rem % m), i1 = (int)((rem / m) % m), i0 = (int)(rem / ((long long)m * m));
+      const int I[3] = {i0, i1, i2};
+      double diag = 0.0;
+      for (int l = 0; l < 3; ++l) {
+        double t = (l == comp) ? beta[b] : alpha[b];
+        for (int k = 0; k < 3; ++k)
+          t *= (double)((k == l) ? bands[(size_t)2 * m * W + I[k] * W + P] : bands[(size_t)I[k] * W + P]);
+        diag += t;
+      }
+      cheb_epi(epi, base + i, rhs[base + i] - v, T(1.0 / diag), ec1, ec2);
+      continue;
+    }
     if (mode == 1) {
       v = rhs[base + i] - v;
       y[base + i] = v;
@@ -750,6 +863,19 @@ size_t apply2d_smem(int m, int P, int TR) {
 }
 
 static constexpr size_t kApplySmemCap = 200 * 1024;
+
+// ---- autotuning table of the 2D apply: (precision bytes, m, P) -> variant
+// 1 = v3 with 16-row tiles, 2 = v3 with 8-row tiles, 3 = v2, 4 = v1 (0 = not tuned).
+// The tuner only chooses between tilings of the same algorithm (FP32: v3 16 vs 8 rows), which
+// compute every output with the same operations in the same order, so the choice never
+// changes a result: solves stay bit-identical across handles, batch sizes and tuning runs.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned;
+static int tuned_variant(size_t es, int m, int P, int /*B*/) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(std::make_tuple((int)es, m, P));
+  return it == g_tuned.end() ? 0 : it->second;
+}
 static int g_use_v2 = 2;  // 2: v3 kernel, 1: v2 kernel, 0: v1 kernel
 void set_apply_variant(int v) { g_use_v2 = v; }
 
@@ -772,8 +898,22 @@ int prepare_kernels() {
 template <typename T>
 int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T* rhs, int mode,
                  int B, Coef c, double* dotp, int* nblk, const int* active, T* scratch,
-                 cudaStream_t s) {
+                 cudaStream_t s, const Epi<T>* epi) {
+  if (mode == 2) {
+    if (!epi) return 1;
+    g_epi<T> = *epi;
+  } else {
+    g_epi<T> = Epi<T>{};
+  }
   if (d == 2) {
+    int tuned = g_use_v2 == 2 ? tuned_variant(sizeof(T), m, P, B) : 0;
+    if (tuned == 1 && try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, 16))
+      return 0;
+    if (tuned == 2 && try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, 8))
+      return 0;
+    if (tuned == 3 && try_apply2d_v2<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+      return 0;
+    if (tuned == 4 && mode != 2) goto plain_v1;
     // FP32: v3 (packed pairs) first; FP64: v2 first (v3's FP64 instantiation is register-bound)
     if (g_use_v2 == 2 && sizeof(T) == 4 &&
         try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
@@ -782,6 +922,8 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
       return 0;
     if (g_use_v2 >= 1 && try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
       return 0;
+  plain_v1:
+    if (mode == 2) return 1;  // the plain kernel has no fused smoother epilogue
     int TR = sizeof(T) == 8 ? 4 : 8;
     while (TR > 1 && apply2d_smem<T>(m, P, TR) > kApplySmemCap) TR /= 2;
     size_t sm = apply2d_smem<T>(m, P, TR);
@@ -794,11 +936,12 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
     return 0;
   }
   const long long N = 3LL * m * m * m;
-  T* ytmp = mode == 1 ? scratch + 18LL * (N / 3) * B : y;
+  T* ytmp = mode >= 1 ? scratch + 18LL * (N / 3) * B : y;
   apply3d_multipass<T>(m, P, bands, w, ytmp, B, c, active, scratch, s);
   const int nb = partial_blocks(N);
-  if (dotp || mode == 1) {
-    post3d_kernel<T><<<dim3(nb, B), 256, 0, s>>>(N, w, ytmp, y, rhs, mode, active, dotp);
+  if (dotp || mode >= 1) {
+    post3d_kernel<T><<<dim3(nb, B), 256, 0, s>>>(N, w, ytmp, y, rhs, mode, active, dotp, m, P,
+                                                  bands, c.alpha, c.beta, g_epi<T>);
     count_launch();
   }
   if (nblk) *nblk = nb;
@@ -807,9 +950,10 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
 
 template int launch_apply<double>(int, int, int, const double*, const double*, double*,
                                   const double*, int, int, Coef, double*, int*, const int*,
-                                  double*, cudaStream_t);
+                                  double*, cudaStream_t, const Epi<double>*);
 template int launch_apply<float>(int, int, int, const float*, const float*, float*, const float*,
-                                 int, int, Coef, double*, int*, const int*, float*, cudaStream_t);
+                                 int, int, Coef, double*, int*, const int*, float*, cudaStream_t,
+                                 const Epi<float>*);
 
 // ------------------------------------------------------------------ reductions and vectors
 template <typename T, typename U>
@@ -855,5 +999,69 @@ int launch_sum_partials(const double* part, int nblk, int B, double* out, cudaSt
   count_launch();
   return 0;
 }
+
+// Times every applicable 2D apply variant on (m, P, B) with CUDA events on stream s (w, y:
+// B-vector buffers; the call must not be inside a stream capture) and records the fastest.
+template <typename T>
+int tune_apply2d(int m, int P, const T* bands, const T* w, T* y, int B, Coef c, cudaStream_t s) {
+  if (g_use_v2 != 2) return 0;
+  const auto key = std::make_tuple((int)sizeof(T), m, P);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;  // first tuning of this shape sticks
+  }
+  if (sizeof(T) == 8) {  // FP64: v2 (no equivalent tiling alternative to time)
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = 3;
+    return 3;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 0;
+  float best = 1e30f;
+  int bestv = 0;
+  for (int v = 1; v <= 2; ++v) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tuned[key] = v;
+    }
+    for (int rep = 0; rep < 2; ++rep)  // warm-up (and first-launch set-up)
+      launch_apply<T>(2, m, P, bands, w, y, nullptr, 0, B, c, nullptr, nullptr, nullptr, nullptr, s);
+    cudaEventRecord(e0, s);
+    int bad = 0;
+    for (int rep = 0; rep < 3; ++rep)
+      bad |= launch_apply<T>(2, m, P, bands, w, y, nullptr, 0, B, c, nullptr, nullptr, nullptr, nullptr, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (bad == 0 && ms < best) {
+      best = ms;
+      bestv = v;
+    }
+  }
+  cudaGetLastError();
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = bestv;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return bestv;
+}
+template int tune_apply2d<float>(int, int, const float*, const float*, float*, int, Coef, cudaStream_t);
+template int tune_apply2d<double>(int, int, const double*, const double*, double*, int, Coef, cudaStream_t);
+
+// Whether launch_apply supports mode 2 (fused smoother epilogue) for this level and batch.
+template <typename T>
+bool apply_can_fuse(int d, int m, int P, const T* bands, int B) {
+  if (d == 3) return true;
+  if (g_use_v2 < 1 || P < 1 || P > 6) return false;
+  StencilHost sh;
+  if (!find_level(bands, sh)) return false;
+  return tuned_variant(sizeof(T), m, P, B) != 4;
+}
+template bool apply_can_fuse<float>(int, int, int, const float*, int);
+template bool apply_can_fuse<double>(int, int, int, const double*, int);
 
 }  // namespace cd

@@ -10,7 +10,6 @@
 namespace cd {
 
 static constexpr int kPowerIts = 14;
-static constexpr double kChebHi = 1.1, kChebRatio = 30.0;
 
 MgData::~MgData() {
   for (void* p : owned) cudaFree(p);
@@ -397,7 +396,8 @@ cd_status mg_build(MgData& mg, int d, int P, const std::vector<int>& ml,
       lb.r = alloc(n * es);
       lb.dv = alloc(n * es);
       lb.dinv = alloc(n * es);
-      if (!lb.b || !lb.x || !lb.r || !lb.dv || !lb.dinv) return CD_ENOMEM;
+      lb.xb = alloc(n * es);
+      if (!lb.b || !lb.x || !lb.r || !lb.dv || !lb.dinv || !lb.xb) return CD_ENOMEM;
     }
   }
   mg.nc = (int)mg.Nl.back();
@@ -516,6 +516,40 @@ static void smooth(MgData& mg, int l, int B, const T* bl, T* xl, bool xzero, Coe
   }
 }
 
+// Degree-2 Chebyshev smoothing with the second step fused into the apply (mode 2).
+// Pre-smoothing from x = 0: X0 = D^{-1} b / theta (= d1), then XB = X0 + d2 with
+// d2 = c1 d1 + c2 D^{-1} (b - A X0).  Post-smoothing from XB: X0 = XB + d1 with
+// d1 = D^{-1} (b - A XB) / theta (d1 -> dv, r0 -> r), then X0 += c1 d1 + c2 D^{-1} (r0 - A d1).
+template <typename T>
+static void smooth_pre_fused(MgData& mg, int l, int B, const T* bl, T* X0, T* XB, Coef c,
+                             const int* active, T* scr, cudaStream_t s) {
+  const int m = mg.ml[l];
+  const long long N = mg.Nl[l];
+  MgLevelBuf& lb = sizeof(T) == 8 ? mg.lv64[l] : mg.lv32[l];
+  const double* lm = mg.lmax + (size_t)l * mg.B;
+  cheb_first_kernel<T><<<grid_for(N, B), 256, 0, s>>>(N, (const T*)lb.dinv, lm, bl, X0, (T*)lb.dv, 1,
+                                                      active);
+  count_launch();
+  Epi<T> e{X0, X0, XB, nullptr, nullptr, lm, 1};
+  launch_apply<T>(mg.d, m, mg.P, level_bands<T>(mg, l), X0, nullptr, bl, 2, B, c, nullptr, nullptr,
+                  active, scr, s, &e);
+}
+
+template <typename T>
+static void smooth_post_fused(MgData& mg, int l, int B, const T* bl, const T* XB, T* X0, Coef c,
+                              const int* active, T* scr, cudaStream_t s) {
+  const int m = mg.ml[l];
+  MgLevelBuf& lb = sizeof(T) == 8 ? mg.lv64[l] : mg.lv32[l];
+  const double* lm = mg.lmax + (size_t)l * mg.B;
+  const T* bands = level_bands<T>(mg, l);
+  Epi<T> e0{nullptr, XB, X0, (T*)lb.dv, (T*)lb.r, lm, 0};
+  launch_apply<T>(mg.d, m, mg.P, bands, XB, nullptr, bl, 2, B, c, nullptr, nullptr, active, scr, s,
+                  &e0);
+  Epi<T> e1{(const T*)lb.dv, X0, X0, nullptr, nullptr, lm, 1};
+  launch_apply<T>(mg.d, m, mg.P, bands, (const T*)lb.dv, nullptr, (const T*)lb.r, 2, B, c, nullptr,
+                  nullptr, active, scr, s, &e1);
+}
+
 template <typename T>
 static void vcycle_rec(MgData& mg, int l, int B, const T* bl, T* xl, Coef c, const int* active,
                        T* fine_scr, cudaStream_t s) {
@@ -528,13 +562,24 @@ static void vcycle_rec(MgData& mg, int l, int B, const T* bl, T* xl, Coef c, con
   }
   MgLevelBuf& lb = sizeof(T) == 8 ? mg.lv64[l] : mg.lv32[l];
   MgLevelBuf& nb = sizeof(T) == 8 ? mg.lv64[l + 1] : mg.lv32[l + 1];
-  smooth<T>(mg, l, B, bl, xl, true, c, active, scr, s);
-  launch_apply<T>(mg.d, mg.ml[l], mg.P, level_bands<T>(mg, l), xl, (T*)lb.r, bl, 1, B, c, nullptr,
+  const bool fused = mg.deg == 2 && apply_can_fuse<T>(mg.d, mg.ml[l], mg.P, level_bands<T>(mg, l), B);
+  T* cur = xl;  // buffer holding the level's iterate after pre-smoothing
+  if (fused) {
+    smooth_pre_fused<T>(mg, l, B, bl, xl, (T*)lb.xb, c, active, scr, s);
+    cur = (T*)lb.xb;
+  } else {
+    smooth<T>(mg, l, B, bl, xl, true, c, active, scr, s);
+  }
+  launch_apply<T>(mg.d, mg.ml[l], mg.P, level_bands<T>(mg, l), cur, (T*)lb.r, bl, 1, B, c, nullptr,
                   nullptr, active, scr, s);
   mg_restrict<T>(mg.d, mg.ml[l], mg.ml[l + 1], B, (const T*)lb.r, (T*)nb.b, active, s);
   vcycle_rec<T>(mg, l + 1, B, (const T*)nb.b, (T*)nb.x, c, active, fine_scr, s);
-  mg_prolong_add<T>(mg.d, mg.ml[l], mg.ml[l + 1], B, (const T*)nb.x, xl, active, s);
-  smooth<T>(mg, l, B, bl, xl, false, c, active, scr, s);
+  mg_prolong_add<T>(mg.d, mg.ml[l], mg.ml[l + 1], B, (const T*)nb.x, cur, active, s);
+  if (fused) {
+    smooth_post_fused<T>(mg, l, B, bl, cur, xl, c, active, scr, s);
+  } else {
+    smooth<T>(mg, l, B, bl, xl, false, c, active, scr, s);
+  }
 }
 
 template <typename T>

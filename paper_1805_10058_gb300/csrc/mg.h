@@ -16,6 +16,7 @@ struct MgLevelBuf {
   void* r = nullptr;  // residual
   void* dv = nullptr;  // Chebyshev direction
   void* dinv = nullptr;  // 1 / diag(A_l) per solve, [B][N_l] (set by mg_prepare)
+  void* xb = nullptr;    // second iterate buffer of the fused smoother (ping-pong)
 };
 
 struct MgData {

@@ -538,6 +538,7 @@ void cd_default_options(cd_options* o) {
   o->chunk = 8;
   o->mixed_switch_ratio = 1e4;
   o->fd_tensor_cores = 1;
+  o->autotune = 1;
 }
 
 size_t cd_dofs(int d, int p, int n) {
@@ -703,6 +704,20 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
                             std::max(1, h->opt.smoother_degree), h->bands64.as<double>(),
                             h->bands32.as<float>(), h->boff);
     if (st != CD_OK) return st;
+  }
+  if (h->opt.autotune && d == 2) {  // pick the 2D apply variant per level and precision
+    std::vector<double> ones(B, 1.0);
+    if (cudaMemcpyAsync(h->alpha.p, ones.data(), 8 * B, cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
+        cudaMemcpyAsync(h->beta.p, ones.data(), 8 * B, cudaMemcpyHostToDevice, h->s) != cudaSuccess) {
+      set_error("autotune set-up failed");
+      return CD_ECUDA;
+    }
+    for (size_t l = 0; l < h->ml.size(); ++l) {
+      tune_apply2d<float>(h->ml[l], P, bands_of<float>(h.get(), l), h->w32.p.as<float>(),
+                          h->w32.q.as<float>(), B, coef_of(h.get()), h->s);
+      tune_apply2d<double>(h->ml[l], P, bands_of<double>(h.get(), l), h->w64.p.as<double>(),
+                           h->w64.q.as<double>(), B, coef_of(h.get()), h->s);
+    }
   }
   if (cudaStreamSynchronize(h->s) != cudaSuccess) {
     set_error(cudaGetErrorString(cudaGetLastError()));

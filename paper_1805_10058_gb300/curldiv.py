@@ -24,7 +24,7 @@ class Options(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("mg_m_min", ctypes.c_int), ("use_graphs", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("mixed_switch_ratio", ctypes.c_double), ("fd_tensor_cores", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class Result(ctypes.Structure):
