@@ -91,6 +91,8 @@ void register_level(const void* bands_dev, int m, int P, int lo, int hi, const d
 void unregister_level(const void* bands_dev);
 // 2D apply kernel: 2 = v3 (x_2 first, packed pairs; default), 1 = v2, 0 = v1.
 void set_apply_variant(int v);
+// 3D apply: 1 = streaming fused kernel (default), 0 = three banded passes (kept for checks).
+void set_apply3d_variant(int v);
 
 // Autotuner of the 2D apply: times the variants on (m, P, B) and records the fastest
 // (returns the chosen variant, 0 if none was tuned).  Not inside a stream capture.

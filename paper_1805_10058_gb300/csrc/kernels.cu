@@ -25,6 +25,8 @@
 
 namespace cd {
 
+static int g_use_stream3d = 1;  // 3D: 1 = streaming fused kernel, 0 = three banded passes
+
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -797,6 +799,235 @@ static int apply3d_multipass(int m, int P, const T* bands, const T* w, T* y, int
   return 0;
 }
 
+// ------------------------------------------------------------------ 3D fused apply
+// One CTA: an (x_3, x_2) tile of 32 x T2 points and a chunk of output planes [k_lo, k_hi)
+// along x_1.  It marches through the input planes q = k_lo - P .. k_hi + P - 1; for each plane
+// it stages the haloed tile of w (3 components) in shared memory, applies the x_3 operators
+// (9 arrays T_{X,c} = X_3 w_c on the tile plus P halo rows of x_2), then each thread forms its
+// point's 9 x_2-results (grouped by the x_1 operator they feed, as in the multi-pass version)
+// and scatters them into a ring of 2P+1 pending output planes:
+//   y_c[k] += M_1(k,q) P_cM[q] + S_1(k,q) P_cS[q] + A_1(k,q) P_cA[q],  |k - q| <= P.
+// Plane k is complete once q = k + P has been handled (or the last plane, near the end of the
+// domain); it then leaves through the epilogue (modes 0, 1, 2) and its slot is cleared.  The
+// slot of plane k is k mod (2P+1): a compile-time index in the plane loop unrolled by 2P+1.
+// Central Toeplitz stencils come from the constant bank, boundary rows from bandT.
+template <typename T>
+__device__ __forceinline__ T band_coef(const Stencil<T>& cs, const T* const* BX, int m, int X,
+                                       int i, int k) {  // X(i, i + k - P)
+  return (i >= cs.lo && i < cs.hi) ? cs.c[X][k] : BX[X][(size_t)k * m + i];
+}
+
+template <typename T, int P, int T2>
+__global__ void __launch_bounds__(32 * T2, 2) apply3d_stream_kernel(
+    int m, int L, const T* __restrict__ bandT, Stencil<T> cs, const T* __restrict__ w,
+    T* __restrict__ y, const T* __restrict__ rhs, int mode, const double* __restrict__ alpha,
+    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp,
+    Epi<T> epi) {
+  constexpr int W = 2 * P + 1, T3 = 32;
+  constexpr int HR = T2 + 2 * P, HC = T3 + 2 * P;
+  const int nchunk = (m + L - 1) / L;
+  const int b = blockIdx.z / nchunk, chunk = blockIdx.z - b * nchunk;
+  if (active && !active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sw = reinterpret_cast<T*>(smem_raw);  // [3][HR][HC]
+  T* st = sw + 3 * HR * HC;                // [9][HR][T3], index X * 3 + c (X: 0 M, 1 A, 2 S)
+  const long long n3 = (long long)m * m * m, N = 3 * n3;
+  const T* wb = w + (long long)b * N;
+  const int i3_0 = blockIdx.x * T3, i2_0 = blockIdx.y * T2;
+  const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+  const int i2 = i2_0 + row, i3 = i3_0 + lane;
+  const bool mine = i2 < m && i3 < m;
+  const int k_lo = chunk * L, k_hi = min(m, k_lo + L);
+  const T al = T(alpha[b]), be = T(beta[b]), ga = T(alpha[b] - beta[b]);
+  const T* BX[3] = {bandT, bandT + (size_t)W * m, bandT + (size_t)2 * W * m};
+  T ec1 = 0, ec2 = 0;
+  if (mode == 2) {
+    double c1, c2;
+    cheb_coef(epi.lmax[b], epi.step, c1, c2);
+    ec1 = T(c1);
+    ec2 = T(c2);
+  }
+  T acc[W][3];
+#pragma unroll
+  for (int sl = 0; sl < W; ++sl) acc[sl][0] = acc[sl][1] = acc[sl][2] = T(0);
+  double dacc = 0.0;
+  const int q_begin = max(0, k_lo - P), q_end = min(m, k_hi + P);
+  for (int qb = (q_begin / W) * W; qb < q_end + P; qb += W) {
+#pragma unroll
+    for (int s = 0; s < W; ++s) {
+      const int q = qb + s;
+      if (q >= q_begin && q < q_end) {  // uniform over the CTA
+        __syncthreads();
+        for (int e = threadIdx.x; e < 3 * HR * HC; e += blockDim.x) {
+          const int c = e / (HR * HC), rem = e - c * HR * HC;
+          const int rr = rem / HC, cc = rem - rr * HC;
+          const int g2 = i2_0 - P + rr, g3 = i3_0 - P + cc;
+          sw[e] = (g2 >= 0 && g2 < m && g3 >= 0 && g3 < m)
+                      ? wb[(long long)c * n3 + ((long long)q * m + g2) * m + g3]
+                      : T(0);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < HR * T3; e += blockDim.x) {  // x_3 operators
+          const int rr = e / T3, cc = e - rr * T3;
+          const int g3 = i3_0 + cc;
+          T t[9];
+#pragma unroll
+          for (int u = 0; u < 9; ++u) t[u] = T(0);
+          if (g3 < m) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+              const T cM = band_coef(cs, BX, m, 0, g3, k), cA = band_coef(cs, BX, m, 1, g3, k),
+                      cS = band_coef(cs, BX, m, 2, g3, k);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                const T v = sw[(c * HR + rr) * HC + cc + k];
+                t[0 * 3 + c] += cM * v;
+                t[1 * 3 + c] += cA * v;
+                t[2 * 3 + c] += cS * v;
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 9; ++u) st[(u * HR + rr) * T3 + cc] = t[u];
+        }
+        __syncthreads();
+        T PM[3], PS[3], PA[3];  // x_2 results of this point, grouped by the x_1 operator
+#pragma unroll
+        for (int c = 0; c < 3; ++c) PM[c] = PS[c] = PA[c] = T(0);
+        if (mine) {
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            const T cM = band_coef(cs, BX, m, 0, i2, k), cA = band_coef(cs, BX, m, 1, i2, k),
+                    cS = band_coef(cs, BX, m, 2, i2, k);
+            const int rr = row + k;
+            const T tM1 = st[(0 * HR + rr) * T3 + lane], tM2 = st[(1 * HR + rr) * T3 + lane];
+            const T tM3 = st[(2 * HR + rr) * T3 + lane], tA1 = st[(3 * HR + rr) * T3 + lane];
+            const T tA2 = st[(4 * HR + rr) * T3 + lane], tA3 = st[(5 * HR + rr) * T3 + lane];
+            const T tS1 = st[(6 * HR + rr) * T3 + lane], tS2 = st[(7 * HR + rr) * T3 + lane];
+            const T tS3 = st[(8 * HR + rr) * T3 + lane];
+            // component 1: M1[alpha (M2 S3 + S2 M3) w1], S1[beta M2 M3 w1], A1[gamma (A2 M3 w2 + M2 A3 w3)]
+            PM[0] += al * (cM * tS1 + cS * tM1);
+            PS[0] += be * (cM * tM1);
+            PA[0] += ga * (cA * tM2 + cM * tA3);
+            // component 2: S1[alpha M2 M3 w2], M1[alpha M2 S3 w2 + beta S2 M3 w2 + gamma A2 A3 w3], A1[gamma A2 M3 w1]
+            PS[1] += al * (cM * tM2);
+            PM[1] += al * (cM * tS2) + be * (cS * tM2) + ga * (cA * tA3);
+            PA[1] += ga * (cA * tM1);
+            // component 3: S1[alpha M2 M3 w3], M1[alpha S2 M3 w3 + beta M2 S3 w3 + gamma A2 A3 w2], A1[gamma M2 A3 w1]
+            PS[2] += al * (cM * tM3);
+            PM[2] += al * (cS * tM3) + be * (cM * tS3) + ga * (cA * tA2);
+            PA[2] += ga * (cM * tA1);
+          }
+        }
+#pragma unroll
+        for (int dd = 0; dd < W; ++dd) {  // x_1 scatter: plane kk = q - (dd - P), column dd
+          const int kk = q - (dd - P);
+          if (kk >= k_lo && kk < k_hi) {
+            constexpr int WW = W;
+            const int slot = ((s - (dd - P)) % WW + WW) % WW;
+            const T cM = band_coef(cs, BX, m, 0, kk, dd), cA = band_coef(cs, BX, m, 1, kk, dd),
+                    cS = band_coef(cs, BX, m, 2, kk, dd);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[slot][c] += cM * PM[c] + cS * PS[c] + cA * PA[c];
+          }
+        }
+      }
+      // plane kd = q - P has received every contribution (q = kd + P, or the last plane m - 1)
+      const int kd = q - P;
+      const int slot = ((s - P) % W + W) % W;
+      if (kd >= k_lo && kd < k_hi && mine) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long o = (long long)b * N + (long long)c * n3 + ((long long)kd * m + i2) * m + i3;
+          const T v = acc[slot][c];
+          if (mode == 2) {
+            const int I[3] = {kd, i2, i3};
+            double diag = 0.0;
+            for (int l = 0; l < 3; ++l) {
+              double tt = (l == c) ? (double)be : (double)al;
+              for (int kx = 0; kx < 3; ++kx)
+                tt *= (double)((kx == l) ? BX[2][(size_t)P * m + I[kx]] : BX[0][(size_t)P * m + I[kx]]);
+              diag += tt;
+            }
+            cheb_epi(epi, o, rhs[o] - v, T(1.0 / diag), ec1, ec2);
+          } else if (mode == 1) {
+            const T r = rhs[o] - v;
+            y[o] = r;
+            dacc += (double)r * (double)r;
+          } else {
+            y[o] = v;
+            if (dotp) dacc += (double)w[o] * (double)v;
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[slot][c] = T(0);
+    }
+  }
+  if (dotp && mode != 2) {
+    const double sum = block_sum(dacc);
+    const int nblk = gridDim.x * gridDim.y * nchunk;
+    const int blk = (chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) dotp[(size_t)b * nblk + blk] = sum;
+  }
+}
+
+template <typename T, int P>
+static size_t stream3d_smem() {
+  constexpr int T2 = 8, HR = T2 + 2 * P, HC = 32 + 2 * P;
+  return sizeof(T) * ((size_t)3 * HR * HC + (size_t)9 * HR * 32);
+}
+
+template <typename T, int P>
+static void launch_stream3d(int m, const T* bands, const StencilHost& sh, const T* w, T* y,
+                            const T* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                            const int* active, cudaStream_t s, const Epi<T>& epi) {
+  Stencil<T> cs;
+  for (int x = 0; x < 3; ++x)
+    for (int k = 0; k < 13; ++k) cs.c[x][k] = k < 2 * P + 1 ? (T)sh.c[x][k] : T(0);
+  cs.lo = sh.lo;
+  cs.hi = sh.hi;
+  constexpr int L = 32;
+  const int nchunk = (m + L - 1) / L;
+  dim3 grid((m + 31) / 32, (m + 7) / 8, nchunk * B);
+  apply3d_stream_kernel<T, P, 8><<<grid, 256, stream3d_smem<T, P>(), s>>>(
+      m, L, bands + (size_t)3 * m * (2 * P + 1), cs, w, y, rhs, mode, c.alpha, c.beta, active,
+      dotp, epi);
+  count_launch();
+  if (nblk) *nblk = grid.x * grid.y * nchunk;
+}
+
+template <typename T>
+static bool try_stream3d(int m, int P, const T* bands, const T* w, T* y, const T* rhs, int mode,
+                         int B, Coef c, double* dotp, int* nblk, const int* active, cudaStream_t s,
+                         const Epi<T>& epi) {
+  // FP32 with p <= 4 only.  The kernel recomputes the x_3 results on the P halo rows of x_2
+  // and the x_2/x_3 results on the P halo planes of each x_1 chunk, about 1.7x the arithmetic
+  // of the three banded passes at p = 3.  FP32 is latency-bound and wins (m = 129: 347 vs
+  // 500 us at p = 3, 154 vs 434 us at p = 2); FP64 is bound by the FP64 pipe (the passes
+  // reach about 1 TFLOP/s) and loses by 3-4x, as does FP32 at p = 5.
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    StencilHost sh;
+    if (!g_use_stream3d || !find_level(bands, sh) || sh.P != P) return false;
+    if ((long long)((m + 31) / 32) * ((m + 7) / 8) * ((m + 31) / 32) > kMaxPartials) return false;
+    switch (P) {
+      case 1: launch_stream3d<T, 1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s, epi); return true;
+      case 2: launch_stream3d<T, 2>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s, epi); return true;
+      case 3: launch_stream3d<T, 3>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s, epi); return true;
+      case 4: launch_stream3d<T, 4>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s, epi); return true;
+      default: return false;
+    }
+  }
+}
+
+template <typename T, int P>
+static void set_stream3d_attr() {
+  cudaFuncSetAttribute(apply3d_stream_kernel<T, P, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)stream3d_smem<T, P>());
+}
+
 // residual / dot post-pass for the multipass 3D apply
 template <typename T>
 __global__ void __launch_bounds__(256) post3d_kernel(long long N, const T* __restrict__ w,
@@ -878,8 +1109,11 @@ static int tuned_variant(size_t es, int m, int P, int /*B*/) {
 }
 static int g_use_v2 = 2;  // 2: v3 kernel, 1: v2 kernel, 0: v1 kernel
 void set_apply_variant(int v) { g_use_v2 = v; }
+void set_apply3d_variant(int v) { g_use_stream3d = v; }
 
 int prepare_kernels() {
+  set_stream3d_attr<float, 1>(); set_stream3d_attr<float, 2>(); set_stream3d_attr<float, 3>();
+  set_stream3d_attr<float, 4>();
   set_v3_attrs<float, 1>(); set_v3_attrs<float, 2>(); set_v3_attrs<float, 3>();
   set_v3_attrs<float, 4>(); set_v3_attrs<float, 5>(); set_v3_attrs<float, 6>();
   set_v3_attrs<double, 1>(); set_v3_attrs<double, 2>(); set_v3_attrs<double, 3>();
@@ -935,6 +1169,8 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
     if (nblk) *nblk = grid.x;
     return 0;
   }
+  if (try_stream3d<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, g_epi<T>))
+    return 0;
   const long long N = 3LL * m * m * m;
   T* ytmp = mode >= 1 ? scratch + 18LL * (N / 3) * B : y;
   apply3d_multipass<T>(m, P, bands, w, ytmp, B, c, active, scratch, s);

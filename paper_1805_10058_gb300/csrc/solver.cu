@@ -669,6 +669,8 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   {
     const char* v = std::getenv("CURLDIV_APPLY_KERNEL");
     set_apply_variant(!v ? 2 : std::string(v) == "v1" ? 0 : std::string(v) == "v2" ? 1 : 2);
+    const char* v3d = std::getenv("CURLDIV_APPLY3D_KERNEL");
+    set_apply3d_variant(v3d && std::string(v3d) == "multipass" ? 0 : 1);
   }
   if (h->opt.precond == CD_PC_FD_D || h->opt.precond == CD_PC_FD_T) {
     cd_status st = ensure_fd(h.get());

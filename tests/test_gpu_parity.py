@@ -38,10 +38,14 @@ APPLY_CASES = [(2, 1, 9), (2, 2, 16), (2, 3, 37), (2, 5, 30), (2, 2, 3), (2, 6, 
 @pytest.mark.parametrize("variant", ["v3", "v2", "v1"])
 @pytest.mark.parametrize("d,p,n", APPLY_CASES)
 def test_apply_fp64_and_fp32_match_oracle(d, p, n, variant, monkeypatch):
-    """Every 2D kernel (v3 default, v2, plain shared-memory v1) against the oracle."""
-    if d == 3 and variant != "v3":
-        pytest.skip("one 3D kernel")
-    monkeypatch.setenv("CURLDIV_APPLY_KERNEL", variant)
+    """Every 2D kernel (v3 default, v2, plain shared-memory v1) and both 3D kernels (streaming
+    default, three banded passes) against the oracle."""
+    if d == 3 and variant == "v1":
+        pytest.skip("two 3D kernels")
+    if d == 3:
+        monkeypatch.setenv("CURLDIV_APPLY3D_KERNEL", "stream" if variant == "v3" else "multipass")
+    else:
+        monkeypatch.setenv("CURLDIV_APPLY_KERNEL", variant)
     alphas = np.array([1.0, 0.5, 3.0])
     betas = np.array([0.1, 7.0, 3.0])
     s = cdl.Solver(d, p, n, max_batch=3)
@@ -73,10 +77,16 @@ def test_apply_full_size_sampled(d, p, n, nsamp):
     y = torch.zeros(s.N, dtype=torch.float64, device="cuda")
     s.cd_apply(dev(w), y, [1.0], [1e-3])
     Y = host(y)
+    w32 = w.astype(np.float32).astype(np.float64)
+    y32 = torch.zeros(s.N, dtype=torch.float32, device="cuda")
+    s.cd_apply_f32(dev(w32, torch.float32), y32, [1.0], [1e-3])
+    Y32 = host(y32)
     rng = np.random.default_rng(0)
     rows = np.concatenate([rng.integers(0, s.N, nsamp), [0, s.N - 1, s.N // d, s.N // d - 1]])
     ref, bound = kron_rows(d, p, n, 1.0, 1e-3, w, rows)
     assert np.all(np.abs(Y[rows] - ref) <= 1e-13 * bound)
+    ref32, bound32 = kron_rows(d, p, n, 1.0, 1e-3, w32, rows)
+    assert np.all(np.abs(Y32[rows] - ref32) <= 3e-5 * bound32)
 
 
 def test_bands_match_oracle_matrices():
@@ -192,6 +202,23 @@ def test_solves_match_oracle(d, p, n, prec, pc):
         assert np.linalg.norm(Bv[k] - A @ X[k]) <= 2e-13 * np.linalg.norm(Bv[k]), res[k]
         assert np.linalg.norm(X[k] - xs) <= 1e-9 * np.linalg.norm(xs), res[k]
         assert res[k]["relres"] <= 1e-13 * 1.01
+
+
+@pytest.mark.parametrize("prec", [cdl.CD_PREC_FP32_IR, cdl.CD_PREC_FP64])
+def test_3d_multigrid_solve_spanning_tiles(prec):
+    """3D, m = 34: several (x_3, x_2) tiles and x_1 chunks of the streaming apply, fused
+    smoother epilogues on every level; residual checked on sampled rows of the oracle."""
+    d, p, n = 3, 2, 34
+    st, res, Bv, X = _solve(d, p, n, [1.0, 1.0], [0.2, 5.0], 2, [3, 4], precision=prec,
+                            precond=cdl.CD_PC_MG, rtol=1e-10)
+    assert st == cdl.CD_OK, res
+    rows = np.random.default_rng(1).integers(0, X.shape[1], 600)
+    for k, beta in enumerate([0.2, 5.0]):
+        ax, _ = kron_rows(d, p, n, 1.0, beta, X[k], rows)
+        r = Bv[k][rows] - ax
+        est = np.sqrt(X.shape[1] / rows.size * np.sum(r ** 2)) / np.linalg.norm(Bv[k])
+        assert est <= 3e-10, est
+        assert res[k]["relres"] <= 1.01e-10
 
 
 def test_config1_plain_cg_fp64():
