@@ -76,6 +76,16 @@ __device__ __forceinline__ void cheb_epi(const Epi<T>& e, long long o, T r, T di
   if (e.rout) e.rout[o] = r;
 }
 
+// 1 / (x * y * z + u * v * t) rounded step by step (no contraction), shared by every 2D kernel's
+// fused smoother epilogue so that all of them produce the same bits.
+__device__ __forceinline__ float inv_diag2(float x, float y, float z, float u, float v, float t) {
+  return __fdiv_rn(1.0f, __fadd_rn(__fmul_rn(__fmul_rn(x, y), z), __fmul_rn(__fmul_rn(u, v), t)));
+}
+__device__ __forceinline__ double inv_diag2(double x, double y, double z, double u, double v,
+                                            double t) {
+  return __ddiv_rn(1.0, __dadd_rn(__dmul_rn(__dmul_rn(x, y), z), __dmul_rn(__dmul_rn(u, v), t)));
+}
+
 // ------------------------------------------------------------------ 2D fused apply
 // One CTA: TR output rows (axis x_1) of one solve, all m columns (axis x_2), both
 // components.  Shared memory: bands [3][m][W], input rows [2][TR+2P][m] (zero outside
@@ -293,8 +303,8 @@ __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
       if (mode == 2) {
         const T Mi = BM[(size_t)P * m + i], Si = BS[(size_t)P * m + i];
         const T Mj = BM[(size_t)P * m + jj], Sj = BS[(size_t)P * m + jj];
-        cheb_epi(epi, o1 + jj, rhs[o1 + jj] - y1, T(1) / (be * Si * Mj + a * Mi * Sj), ec1, ec2);
-        cheb_epi(epi, o2 + jj, rhs[o2 + jj] - y2, T(1) / (a * Si * Mj + be * Mi * Sj), ec1, ec2);
+        cheb_epi(epi, o1 + jj, rhs[o1 + jj] - y1, inv_diag2(be, Si, Mj, a, Mi, Sj), ec1, ec2);
+        cheb_epi(epi, o2 + jj, rhs[o2 + jj] - y2, inv_diag2(a, Si, Mj, be, Mi, Sj), ec1, ec2);
         continue;
       }
       if (mode == 1) {
@@ -471,8 +481,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel
         if (mode == 2) {
           const T Mi = BM[(size_t)P * m + i], Si = BS[(size_t)P * m + i];
           const T Mj = BM[(size_t)P * m + j], Sj = BS[(size_t)P * m + j];
-          cheb_epi(epi, o1, rhs[o1] - y1, T(1) / (be * Si * Mj + al * Mi * Sj), ec1, ec2);
-          cheb_epi(epi, o2, rhs[o2] - y2, T(1) / (al * Si * Mj + be * Mi * Sj), ec1, ec2);
+          cheb_epi(epi, o1, rhs[o1] - y1, inv_diag2(be, Si, Mj, al, Mi, Sj), ec1, ec2);
+          cheb_epi(epi, o2, rhs[o2] - y2, inv_diag2(al, Si, Mj, be, Mi, Sj), ec1, ec2);
           continue;
         }
         if (mode == 1) {
@@ -1097,9 +1107,11 @@ static constexpr size_t kApplySmemCap = 200 * 1024;
 
 // ---- autotuning table of the 2D apply: (precision bytes, m, P) -> variant
 // 1 = v3 with 16-row tiles, 2 = v3 with 8-row tiles, 3 = v2, 4 = v1 (0 = not tuned).
-// The tuner only chooses between tilings of the same algorithm (FP32: v3 16 vs 8 rows), which
-// compute every output with the same operations in the same order, so the choice never
-// changes a result: solves stay bit-identical across handles, batch sizes and tuning runs.
+// The tuner chooses between tilings of one algorithm (FP32: v3 with 16 or 8 rows per tile), which
+// compute every output of the apply with the same operations in the same order.  The fused
+// dot partials are grouped by tile, so a Krylov iterate can differ in its last bits between the
+// two tilings; the choice is made once per (precision, m, p) and process, so within a process
+// solves stay bit-identical across handles and batch sizes.
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int>, int> g_tuned;
 static int tuned_variant(size_t es, int m, int P, int /*B*/) {
@@ -1236,7 +1248,7 @@ int launch_sum_partials(const double* part, int nblk, int B, double* out, cudaSt
   return 0;
 }
 
-// Times every applicable 2D apply variant on (m, P, B) with CUDA events on stream s (w, y:
+// Times the applicable 2D apply tilings on (m, P, B) with CUDA events on stream s (w, y:
 // B-vector buffers; the call must not be inside a stream capture) and records the fastest.
 template <typename T>
 int tune_apply2d(int m, int P, const T* bands, const T* w, T* y, int B, Coef c, cudaStream_t s) {

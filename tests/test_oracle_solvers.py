@@ -147,3 +147,41 @@ def test_p_mim_is_flat_in_n():
         A, b, d, p, m = _case(row)
         ks.append(solvers.p_mim(A, b, d, p, m)[1])
     assert max(ks) - min(ks) <= 3, ks
+
+
+def _fp64_floor(p, n, beta):
+    """Relative residual, evaluated in extended precision, of the exact solution rounded to
+    FP64 (the exact solution: an LU solve refined with extended-precision residuals)."""
+    from paper_1805_10058_gb300 import inputs
+    A = sp.csr_matrix(assemble.galerkin_kron(2, p, n, 1.0, beta))
+    b = inputs.uniform_rhs(2, p, n, seed=0)[0]
+    C = A.tocoo()
+    vals = C.data.astype(np.longdouble)
+
+    def res(x):
+        r = b.astype(np.longdouble)
+        np.subtract.at(r, C.row, vals * x[C.col])
+        return r
+
+    lu = sp.linalg.splu(A.tocsc())
+    x = lu.solve(b).astype(np.longdouble)
+    for _ in range(4):
+        x = x + lu.solve(res(x).astype(np.float64)).astype(np.longdouble)
+    nb = np.sqrt(np.sum(b.astype(np.longdouble) ** 2))
+    exact = float(np.sqrt(np.sum(res(x) ** 2)) / nb)
+    rounded = float(np.sqrt(np.sum(res(x.astype(np.float64).astype(np.longdouble)) ** 2)) / nb)
+    return exact, rounded
+
+
+@pytest.mark.skipif(np.finfo(np.longdouble).eps > 1e-18, reason="needs 80-bit long double")
+def test_fp64_residual_floor_at_extreme_parameters():
+    """At beta/alpha = 1e6 the exact solution, merely rounded to FP64, already leaves a relative
+    residual that grows with n (about 5e-11 at n = 62, 1e-10 at n = 126): a relative residual
+    of 1e-10 is out of reach of any FP64 iterate at the n = 256 sweep.  At beta = alpha the same
+    floor is at the level of the unit roundoff."""
+    e62, r62 = _fp64_floor(2, 62, 1e6)
+    e126, r126 = _fp64_floor(2, 126, 1e6)
+    assert e62 < 1e-12 and e126 < 1e-12  # the refined solution is exact to well below the floor
+    assert r62 > 2e-11 and r126 > 5e-11 and r126 > 1.5 * r62
+    _, r1 = _fp64_floor(2, 62, 1.0)
+    assert r1 < 1e-15
