@@ -599,7 +599,7 @@ static bool try_apply2d_v3(int m, int P, const T* bands, const T* w, T* y, const
                            cudaStream_t s, int TR = 0) {
   StencilHost sh;
   if (!find_level(bands, sh) || sh.P != P) return false;
-  if ((long long)((m + 63) / 64) * ((m + 7) / 8) > kMaxPartials) return false;
+  if (dotp && (long long)((m + 63) / 64) * ((m + 7) / 8) > kMaxPartials) return false;
   if (TR == 8 || TR == 16) {
     switch (P) {
       case 1: return try_v3_P_tr<T, 1>(TR, m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
@@ -1021,7 +1021,8 @@ static bool try_stream3d(int m, int P, const T* bands, const T* w, T* y, const T
   } else {
     StencilHost sh;
     if (!g_use_stream3d || !find_level(bands, sh) || sh.P != P) return false;
-    if ((long long)((m + 31) / 32) * ((m + 7) / 8) * ((m + 31) / 32) > kMaxPartials) return false;
+    if (dotp && (long long)((m + 31) / 32) * ((m + 7) / 8) * ((m + 31) / 32) > kMaxPartials)
+      return false;
     switch (P) {
       case 1: launch_stream3d<T, 1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s, epi); return true;
       case 2: launch_stream3d<T, 2>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s, epi); return true;
@@ -1145,6 +1146,23 @@ template <typename T>
 int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T* rhs, int mode,
                  int B, Coef c, double* dotp, int* nblk, const int* active, T* scratch,
                  cudaStream_t s, const Epi<T>* epi) {
+  // Very large grids have more tiles than dot-partial slots: the apply then runs without its
+  // fused partials and the fixed-order dot kernel supplies them (per solve, independent of the
+  // batch, like the fused ones).
+  if (dotp && mode != 2) {
+    const long long tiles = d == 2 ? (long long)((m + 63) / 64) * ((m + 7) / 8)
+                                   : (long long)((m + 31) / 32) * ((m + 7) / 8) * ((m + 31) / 32);
+    if (tiles > kMaxPartials) {
+      const int r = launch_apply<T>(d, m, P, bands, w, y, rhs, mode, B, c, nullptr, nullptr,
+                                    active, scratch, s, epi);
+      if (r != 0) return r;
+      const long long N = d == 2 ? 2LL * m * m : 3LL * m * m * m;
+      const int nb = partial_blocks(N);
+      launch_dot<T>(mode == 1 ? y : w, y, N, B, dotp, nb, active, s);
+      if (nblk) *nblk = nb;
+      return 0;
+    }
+  }
   if (mode == 2) {
     if (!epi) return 1;
     g_epi<T> = *epi;
@@ -1173,7 +1191,7 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
     int TR = sizeof(T) == 8 ? 4 : 8;
     while (TR > 1 && apply2d_smem<T>(m, P, TR) > kApplySmemCap) TR /= 2;
     size_t sm = apply2d_smem<T>(m, P, TR);
-    if (sm > kApplySmemCap || (m + TR - 1) / TR > kMaxPartials) return 1;  // too large for v1
+    if (sm > kApplySmemCap || (dotp && (m + TR - 1) / TR > kMaxPartials)) return 1;  // too large for v1
     dim3 grid((m + TR - 1) / TR, B);
     apply2d_kernel<T><<<grid, 256, sm, s>>>(m, P, TR, bands, w, y, rhs, mode, c.alpha, c.beta,
                                             active, dotp);

@@ -44,13 +44,17 @@ def kron_rows(d, p, n, alpha, beta, w, rows):
             else:
                 terms = [(alpha, t) for t in curl[c][c2]] + [(beta, t) for t in div[c][c2]]
             for coef, mats in terms:
+                # each 1D row is banded: contract over its nonzero window only
                 rowv = [mats[l][idx[l], :] for l in range(d)]
+                nz = [np.nonzero(v)[0] for v in rowv]
+                sub = W[c2][np.ix_(*nz)]
+                rv = [rowv[l][nz[l]] for l in range(d)]
                 if d == 2:
-                    t = np.einsum("i,j,ij->", rowv[0], rowv[1], W[c2])
-                    at = np.einsum("i,j,ij->", np.abs(rowv[0]), np.abs(rowv[1]), np.abs(W[c2]))
+                    t = np.einsum("i,j,ij->", rv[0], rv[1], sub)
+                    at = np.einsum("i,j,ij->", np.abs(rv[0]), np.abs(rv[1]), np.abs(sub))
                 else:
-                    t = np.einsum("i,j,k,ijk->", rowv[0], rowv[1], rowv[2], W[c2])
-                    at = np.einsum("i,j,k,ijk->", *[np.abs(x) for x in rowv], np.abs(W[c2]))
+                    t = np.einsum("i,j,k,ijk->", rv[0], rv[1], rv[2], sub)
+                    at = np.einsum("i,j,k,ijk->", *[np.abs(x) for x in rv], np.abs(sub))
                 tot += coef * t
                 atot += abs(coef) * at
         out[k] = tot

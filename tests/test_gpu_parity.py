@@ -89,6 +89,39 @@ def test_apply_full_size_sampled(d, p, n, nsamp):
     assert np.all(np.abs(Y32[rows] - ref32) <= 3e-5 * bound32)
 
 
+def test_2d_large_grid_beyond_fused_partials():
+    """m = 2047 (8.4M unknowns per solve): more apply tiles than fused dot-partial slots, so the
+    apply runs without them and the dot kernel supplies the partials.  Sampled rows of the FP64
+    and FP32 apply against the oracle's 1D matrices, then a multigrid solve of two right-hand
+    sides whose true residual is estimated from sampled rows."""
+    d, p, n = 2, 3, 2046
+    s = cdl.Solver(d, p, n, max_batch=2, precision=cdl.CD_PREC_FP32_IR, precond=cdl.CD_PC_MG,
+                   rtol=1e-9, maxit=3000)
+    w = inputs.uniform_rhs(d, p, n, seed=5)[0]
+    y = torch.zeros(s.N, dtype=torch.float64, device="cuda")
+    s.cd_apply(dev(w), y, [1.0], [0.3])
+    w32 = w.astype(np.float32).astype(np.float64)
+    y32 = torch.zeros(s.N, dtype=torch.float32, device="cuda")
+    s.cd_apply_f32(dev(w32, torch.float32), y32, [1.0], [0.3])
+    rng = np.random.default_rng(2)
+    rows = np.concatenate([rng.integers(0, s.N, 300), [0, s.N - 1, s.N // 2, s.N // 2 - 1]])
+    ref, bound = kron_rows(d, p, n, 1.0, 0.3, w, rows)
+    assert np.all(np.abs(host(y)[rows] - ref) <= 1e-13 * bound)
+    ref32, bound32 = kron_rows(d, p, n, 1.0, 0.3, w32, rows)
+    assert np.all(np.abs(host(y32)[rows] - ref32) <= 3e-5 * bound32)
+    Bv = inputs.uniform_rhs_seeds(d, p, n, [0, 1])
+    x = torch.zeros(2 * s.N, dtype=torch.float64, device="cuda")
+    st, res = s.cd_solve(dev(Bv.ravel()), x, [1.0, 1.0], [1.0, 0.3], check=False)
+    assert st == cdl.CD_OK, res
+    X = host(x).reshape(2, -1)
+    for k, beta in enumerate([1.0, 0.3]):
+        assert res[k]["relres"] <= 1e-9
+        ax, _ = kron_rows(d, p, n, 1.0, beta, X[k], rows)
+        r = Bv[k][rows] - ax
+        est = np.sqrt(s.N / rows.size * np.sum(r ** 2)) / np.linalg.norm(Bv[k])
+        assert est <= 3e-9, est
+
+
 def test_bands_match_oracle_matrices():
     for p, n in [(1, 8), (2, 16), (3, 37), (5, 20)]:
         s = cdl.Solver(2, p, n, max_batch=1)
