@@ -93,6 +93,7 @@ void unregister_level(const void* bands_dev);
 void set_apply_variant(int v);
 // 3D apply: 1 = streaming fused kernel (default), 0 = three banded passes (kept for checks).
 void set_apply3d_variant(int v);
+void set_apply_fp64_variant(int v);  // 2D FP64: 0 = v2, 1 = v3
 
 // Autotuner of the 2D apply: times the variants on (m, P, B) and records the fastest
 // (returns the chosen variant, 0 if none was tuned).  Not inside a stream capture.

@@ -1,18 +1,28 @@
 // Fast-diagonalisation contractions on the 5th-generation tensor cores (tcgen05, sm_103a).
 //
-// C[z](r, c) = sum_k A[z](r, k) B[z](k, c) for one axis of the FD transform (see
-// launch_fd_axis): FP32 operands read as TF32 by tcgen05.mma kind::tf32, FP32 accumulation in
-// tensor memory.  One CTA (4 warps) owns a 128 x 128 output tile; K (= m) is consumed in
-// chunks of 32 staged into shared memory in the canonical K-major layout without swizzle
-// (8-row x 16-byte core matrices; leading-byte offset = next core matrix along K, stride-byte
-// offset = next 8-row group), double-buffered.  Thread 0 issues the MMAs and commits them to an
-// mbarrier; the epilogue reads the accumulator with tcgen05.ld and applies the FD eigenvalue
-// scaling.  The tensors' rows are m floats long (m odd for most (p, n)), which TMA's 16-byte
-// stride rule excludes, so the CTA stages its tiles itself (coalesced global loads).
+// One axis of the FD transform (see launch_fd_axis) as C(R, n) = sum_k A(R, k) B(n, k):
+// R runs over the accumulator's rows (tensor-memory lanes), n over the eigen index along the
+// axis (the MMA's N, a multiple of 16 up to 256 chosen per launch so that m is covered with
+// little padding), k over the contraction (= m).  FP32 operands are read as TF32 by
+// tcgen05.mma kind::tf32, with FP32 accumulation in tensor memory.  One CTA (4 warps) owns 128
+// rows and one N tile; K is consumed in chunks of 32 staged into shared memory in the canonical
+// K-major layout without swizzle (8-row x 16-byte core matrices; leading-byte offset = next core
+// matrix along K, stride-byte offset = next 8-row group), double-buffered.  Thread 0 issues the
+// MMAs and commits them to an mbarrier; the epilogue reads the accumulator with tcgen05.ld and
+// applies the FD eigenvalue scaling.  The tensors' rows are m floats long (m odd for most
+// (p, n)), which TMA's 16-byte stride rule excludes, so the CTA stages its tiles itself: a warp
+// fills one 128-byte core matrix per step (conflict-free shared stores), its lanes ordered along
+// whichever operand index is contiguous in global memory.
+//
+// Orientation: for an axis other than the last, R = (block, position along the later axes),
+// the unit-stride index of the output, so a warp's stores are contiguous; blocks are merged
+// into one row range so that tiles do not restart per block.  For the last axis R is the data
+// row and the output's unit stride is n: the epilogue transposes through shared memory.
 // Every mbarrier wait is bounded; on expiry the kernel raises *err and skips its stores.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 
 #include "krylov.h"
@@ -20,17 +30,22 @@
 namespace cd {
 
 namespace {
-constexpr int TM = 128, TN = 128, KC = 32;                  // tile and K chunk
-constexpr int A_BYTES = TM * KC * 4, B_BYTES = TN * KC * 4;  // 16 KB each
+constexpr int TM = 128, KC = 32, TN_MAX = 144, NST = 3;  // row tile, K chunk, N cap, stages
+constexpr int NW = 8, NTHR = 32 * NW;                    // warps, threads per CTA
+constexpr int A_BYTES = TM * KC * 4;                     // 16 KB
+constexpr int EPI_BYTES = NW * 32 * 65 * 4;              // transposing epilogue, per CTA
+constexpr int MAX_SMEM = NST * (A_BYTES + TN_MAX * KC * 4);  // 102 KB at N = 144
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Byte offset of element (row, k) inside a [rows x KC] K-major no-swizzle chunk.
-__device__ __forceinline__ uint32_t core_off(int row, int k) {
-  return (uint32_t)(((row >> 3) * (KC / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+// 4-byte asynchronous global -> shared copy; zero-filled when !valid (src is not read)
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
@@ -43,9 +58,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;                // base offset 0, no swizzle
 }
 
-// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
+// kind::tf32 instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = tn
+__device__ __forceinline__ uint32_t idesc_tf32(int tn) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(tn >> 3) << 17) |
+         ((uint32_t)(TM >> 4) << 24);
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
@@ -67,32 +84,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 }
 }  // namespace
 
-template <typename T>
-__global__ void __launch_bounds__(128, 1) fd_tc_kernel(int Mr, int Nc, int K, const float* __restrict__ A,
-                                                       long long ars, long long acs, long long abs_,
-                                                       const float* __restrict__ Bm, long long brs,
-                                                       long long bcs, long long bbs, float* __restrict__ C,
-                                                       long long crs, long long ccs, long long cbs,
-                                                       FdScale<float> sc, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[2];
-  __shared__ uint32_t tmem_base_sh;
-  const int z = blockIdx.z;
-  const int r0 = blockIdx.y * TM, c0 = blockIdx.x * TN;
-  const float* Az = A + (long long)z * abs_;
-  const float* Bz = Bm + (long long)z * bbs;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  unsigned char* bufA[2] = {smem, smem + A_BYTES + B_BYTES};
-  unsigned char* bufB[2] = {smem + A_BYTES, smem + 2 * A_BYTES + B_BYTES};
+// C(R, n) = sum_k A(R, k) B(n, k); row R = z * Ia + c (block z, position c).
+struct FdTcArgs {
+  int M, N, K, TN, Ia;
+  long long a_zs, a_rs, a_ks;  // A(R, k) at A[z * a_zs + c * a_rs + k * a_ks]
+  long long b_ns, b_ks;        // B(n, k) at B[n * b_ns + k * b_ks]
+  long long c_zs, c_rs, c_ns;  // C(R, n) at C[z * c_zs + c * c_rs + n * c_ns]
+  const float* A;
+  const float* B;
+  float* C;
+};
 
-  if (warp == 0) {  // tensor-memory allocation: 128 FP32 columns = the 128 x 128 accumulator
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+__global__ void __launch_bounds__(NTHR, 1) fd_tc_kernel(FdTcArgs g, FdScale<float> sc,
+                                                        int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[NST];
+  __shared__ uint32_t tmem_base_sh;
+  const int r0 = blockIdx.x * TM, c0 = blockIdx.y * g.TN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {  // tensor-memory allocation: 256 FP32 columns (the N tile is <= 144)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
                      smem_u32(&tmem_base_sh)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int i = 0; i < NST; ++i) mbar_init(&bars[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -100,55 +117,95 @@ __global__ void __launch_bounds__(128, 1) fd_tc_kernel(int Mr, int Nc, int K, co
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_sh;
 
-  const int nchunks = (K + KC - 1) / KC;
-  uint32_t phase[2] = {0, 0};
-  bool ok = true;
-  for (int ch = 0; ch < nchunks; ++ch) {
-    const int buf = ch & 1;
-    // the MMAs that read this buffer two chunks ago must be complete before it is rewritten
-    if (ch >= 2) {
-      if (!mbar_wait(&bars[buf], phase[buf])) ok = false;
-      phase[buf] ^= 1;
+  // staging roles, fixed over K: this thread's rows of A (2 of the 16 row groups) and of B (up
+  // to 3 of at most 18), each with its source pointer at k = its lane's k offset
+  const int rowsA = (min(TM, g.M - r0) + 7) & ~7, rowsB = (min(g.TN, g.N - c0) + 7) & ~7;
+  const bool a_kfast = g.a_ks == 1, b_kfast = g.b_ks == 1;
+  const int a_r8 = a_kfast ? (lane >> 2) : (lane & 7), a_k4 = a_kfast ? (lane & 3) : (lane >> 3);
+  const int b_r8 = b_kfast ? (lane >> 2) : (lane & 7), b_k4 = b_kfast ? (lane & 3) : (lane >> 3);
+  const float* pA[2];
+  bool aok[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int R = r0 + (warp + NW * i) * 8 + a_r8;
+    aok[i] = R < g.M;
+    const int z = aok[i] ? R / g.Ia : 0;
+    pA[i] = aok[i] ? g.A + (long long)z * g.a_zs + (long long)(R - z * g.Ia) * g.a_rs +
+                         (long long)a_k4 * g.a_ks
+                   : g.A;
+  }
+  const float* pB[3];
+  bool bok[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int n = c0 + (warp + NW * i) * 8 + b_r8;
+    bok[i] = n < g.N;
+    pB[i] = bok[i] ? g.B + (long long)n * g.b_ns + (long long)b_k4 * g.b_ks : g.B;
+  }
+
+  const int nchunks = (g.K + KC - 1) / KC;
+  const uint32_t idesc = idesc_tf32(g.TN);
+  const int stage_bytes = A_BYTES + g.TN * KC * 4;
+  const uint32_t smem0 = smem_u32(smem);
+  // Issues this thread's copies of K chunk ch into stage st (rows past the matrix edge are not
+  // staged: they only feed accumulator rows / columns that are never stored; the K tail is
+  // zero-filled).
+  auto issue_rows = [&](const float* p0, bool rok, long long ks, uint32_t dst, int k0, int k4) {
+    if (k0 + KC <= g.K) {
+      const long long step = rok ? 4 * ks : 0;
+      const float* p = rok ? p0 + (long long)k0 * ks : p0;
+#pragma unroll
+      for (int kb = 0; kb < KC / 4; ++kb) {
+        cp_async4(dst + kb * 128, p, rok);
+        p += step;
+      }
+    } else {
+#pragma unroll
+      for (int kb = 0; kb < KC / 4; ++kb) {
+        const bool v = rok && k0 + kb * 4 + k4 < g.K;
+        cp_async4(dst + kb * 128, v ? p0 + (long long)(k0 + kb * 4) * ks : p0, v);
+      }
     }
+  };
+  auto issue_chunk = [&](int ch, int st) {
     const int k0 = ch * KC;
-    // stage A chunk [TM x KC] and B chunk [TN x KC] (as (row = c, k)) in the core layout
-    if (acs == 1) {  // lanes cover one 8-row x 4-float core block: conflict-free stores
-      for (int e = tid; e < TM * KC; e += 128) {
-        const int blk = e >> 5, kk = (blk % (KC / 4)) * 4 + (e & 3);
-        const int rr = (blk / (KC / 4)) * 8 + ((e >> 2) & 7);
-        const int gr = r0 + rr, gk = k0 + kk;
-        const float v = (gr < Mr && gk < K) ? Az[gr * ars + gk] : 0.f;
-        *reinterpret_cast<float*>(bufA[buf] + core_off(rr, kk)) = v;
-      }
-    } else {
-      for (int e = tid; e < TM * KC; e += 128) {
-        const int rr = e % TM, kk = e / TM;
-        const int gr = r0 + rr, gk = k0 + kk;
-        const float v = (gr < Mr && gk < K) ? Az[gr * ars + gk * acs] : 0.f;
-        *reinterpret_cast<float*>(bufA[buf] + core_off(rr, kk)) = v;
-      }
+    const uint32_t sA = smem0 + st * stage_bytes, sB = sA + A_BYTES;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int rb = warp + NW * i;
+      if (rb * 8 >= rowsA) break;
+      issue_rows(pA[i], aok[i], g.a_ks, sA + rb * (KC / 4) * 128 + a_r8 * 16 + a_k4 * 4, k0, a_k4);
     }
-    if (bcs == 1) {
-      for (int e = tid; e < TN * KC; e += 128) {
-        const int cc = e % TN, kk = e / TN;
-        const int gc = c0 + cc, gk = k0 + kk;
-        const float v = (gc < Nc && gk < K) ? Bz[gk * brs + gc] : 0.f;
-        *reinterpret_cast<float*>(bufB[buf] + core_off(cc, kk)) = v;
-      }
-    } else {
-      for (int e = tid; e < TN * KC; e += 128) {
-        const int cc = e / KC, kk = e % KC;
-        const int gc = c0 + cc, gk = k0 + kk;
-        const float v = (gc < Nc && gk < K) ? Bz[gk * brs + gc * bcs] : 0.f;
-        *reinterpret_cast<float*>(bufB[buf] + core_off(cc, kk)) = v;
-      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int rb = warp + NW * i;
+      if (rb * 8 >= rowsB) break;
+      issue_rows(pB[i], bok[i], g.b_ks, sB + rb * (KC / 4) * 128 + b_r8 * 16 + b_k4 * 4, k0, b_k4);
     }
+  };
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < NST - 1; ++c) {
+    if (c < nchunks) issue_chunk(c, c);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int st = ch % NST;
+    // refill the stage of chunk ch - 1 with chunk ch + NST - 1 once its MMAs have completed
+    const int nxt = ch + NST - 1;
+    if (nxt < nchunks) {
+      const int sn = nxt % NST;
+      if (nxt >= NST && !mbar_wait(&bars[sn], ((nxt - NST) / NST) & 1)) ok = false;
+      issue_chunk(nxt, sn);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NST - 1) : "memory");  // chunk ch landed
     // generic-proxy writes -> visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(bufA[buf]), b0 = smem_u32(bufB[buf]);
+      const uint32_t a0 = smem0 + st * stage_bytes, b0 = a0 + A_BYTES;
 #pragma unroll
       for (int s = 0; s < KC / 8; ++s) {  // K = 8 per MMA = two 16-byte core matrices
         const uint64_t ad = smem_desc(a0 + s * 256), bd = smem_desc(b0 + s * 256);
@@ -156,72 +213,113 @@ __global__ void __launch_bounds__(128, 1) fd_tc_kernel(int Mr, int Nc, int K, co
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&bars[buf])));
+              smem_u32(&bars[st])));
     }
   }
-  // wait for the last commit of each buffer in use
-  {
-    const int lastbuf = (nchunks - 1) & 1;
-    if (!mbar_wait(&bars[lastbuf], phase[lastbuf])) ok = false;
-    if (nchunks >= 2) {
-      const int other = lastbuf ^ 1;
-      if (!mbar_wait(&bars[other], phase[other])) ok = false;
-    }
-  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  // the last commit tracks every MMA issued before it
+  if (!mbar_wait(&bars[(nchunks - 1) % NST], ((nchunks - 1) / NST) & 1)) ok = false;
   asm volatile("tcgen05.fence::after_thread_sync;");
-  // epilogue: warp w reads accumulator lanes 32w..32w+31 (one output row per thread)
-  const int row = r0 + warp * 32 + (tid & 31);
-  float* Cz = C + (long long)z * cbs;
-  if (!ok) {
-    if (tid == 0) atomicExch(err, 1);
-  }
-#pragma unroll 1
-  for (int cb = 0; cb < TN; cb += 8) {
-    uint32_t v[8];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-    if (ok && row < Mr) {
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int col = c0 + cb + j;
-        if (col >= Nc) continue;
-        float out = __uint_as_float(v[j]);
-        float* dst = Cz + (long long)row * crs + (long long)col * ccs;
-        if (sc.mode) {
-          long long off = dst - sc.base;
-          const long long bc = off / sc.per;
-          long long rem = off - bc * sc.per;
-          const int bsol = (int)(bc / sc.d), comp = (int)(bc % sc.d);
-          double den = sc.mode == 1 ? 0.0 : 1.0;
-          for (int l = sc.d - 1; l >= 0; --l) {
-            const int kl = (int)(rem % sc.m);
-            rem /= sc.m;
-            const double lam = (double)sc.lam[kl];
-            if (sc.mode == 1)
-              den += (l == comp ? sc.beta[bsol] : sc.alpha[bsol]) * lam;
-            else
-              den *= lam;
-          }
-          out = (float)((double)out / den);
-        }
-        *dst = out;
+  if (!ok && tid == 0) atomicExch(err, 1);
+  const int ncol = min(g.TN, g.N - c0);
+  // two warps per 32-lane quarter of the accumulator (a warp may read only its own quarter,
+  // warp % 4); they split the columns
+  const int quarter = warp & 3, half = warp >> 2;
+  const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16);
+  if (g.c_rs == 1) {
+    // direct: this thread's row R is the output's unit-stride index
+    const int R = r0 + quarter * 32 + lane;
+    const bool rok = R < g.M;
+    const int z = rok ? R / g.Ia : 0, c = rok ? R - z * g.Ia : 0;
+    float* crow = g.C + (long long)z * g.c_zs + c;
+    // FD scaling (forward pass along axis 0): the row is the flat index of axes 1..d-1 inside
+    // block z = (solve, component), the columns the axis-0 eigen index; the row's part of the
+    // eigenvalue sum (FD-D) or product (FD-T) is formed once.
+    double srow = 0.0, coef0 = 1.0;
+    if (sc.mode && rok) {
+      const int bsol = z / sc.d, comp = z - bsol * sc.d;
+      int rem = c;
+      srow = sc.mode == 1 ? 0.0 : 1.0;
+      for (int l = sc.d - 1; l >= 1; --l) {
+        const int kl = rem % sc.m;
+        rem /= sc.m;
+        const double lam = (double)sc.lam[kl];
+        if (sc.mode == 1)
+          srow += (l == comp ? sc.beta[bsol] : sc.alpha[bsol]) * lam;
+        else
+          srow *= lam;
       }
+      if (sc.mode == 1) coef0 = comp == 0 ? sc.beta[bsol] : sc.alpha[bsol];
+    }
+#pragma unroll 1
+    for (int cb = 8 * half; cb < ncol; cb += 16) {
+      uint32_t v[8];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7])
+          : "r"(tbase + (uint32_t)cb));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (ok && rok) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (cb + j >= ncol) break;
+          const int n = c0 + cb + j;
+          float out = __uint_as_float(v[j]);
+          if (sc.mode) {
+            const double lam0 = (double)sc.lam[n];
+            const double den = sc.mode == 1 ? srow + coef0 * lam0 : srow * lam0;
+            out = (float)((double)out / den);
+          }
+          crow[(long long)n * g.c_ns] = out;
+        }
+      }
+    }
+  } else {
+    // transposed through shared memory (the staging buffers are free now): a warp moves 32 rows
+    // x 64 columns at a time and stores each row's columns contiguously
+    __syncthreads();
+    float* sm = reinterpret_cast<float*>(smem) + warp * (32 * 65);
+#pragma unroll 1
+    for (int cb0 = 64 * half; cb0 < ncol; cb0 += 128) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint32_t v[8];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7])
+            : "r"(tbase + (uint32_t)(cb0 + 8 * q)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sm[lane * 65 + 8 * q + j] = __uint_as_float(v[j]);
+      }
+      __syncwarp();
+      if (ok) {
+        for (int rr = 0; rr < 32; ++rr) {
+          const int R = r0 + quarter * 32 + rr;
+          if (R >= g.M) break;
+          const int z = g.Ia == INT_MAX ? 0 : R / g.Ia, c = R - z * g.Ia;
+          float* crow = g.C + (long long)z * g.c_zs + (long long)c * g.c_rs;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int cc = cb0 + lane + 32 * h;
+            if (cc < ncol) crow[(long long)(c0 + cc) * g.c_ns] = sm[rr * 65 + lane + 32 * h];
+          }
+        }
+      }
+      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   }
 }
 
@@ -238,33 +336,53 @@ bool launch_fd_axis_tc(int d, int m, int axis, int B, const float* G, const floa
   for (int l = axis + 1; l < d; ++l) I *= m;
   long long O = (long long)B * d;
   for (int l = 0; l < axis; ++l) O *= m;
-  const size_t smem = 2 * (A_BYTES + B_BYTES);
+  if (sc.mode && I == 1) return false;  // the scaling epilogue expects an axis before the last
+  if (O * I > INT_MAX) return false;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(fd_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(fd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
     attr = true;
   }
+  // N tile: cover m with as few tiles of at most 144 as possible, each a multiple of 16 (at
+  // 144, three stages of operands take 102 KB: two CTAs per SM)
+  const int nt = (m + 143) / 144;
+  const int tn = std::max(16, ((m + nt - 1) / nt + 15) / 16 * 16);
+  FdTcArgs g{};
+  g.N = m;
+  g.K = m;
+  g.TN = tn;
+  g.B = G;  // G[k * m + n]: the eigen index n of the output at unit stride
+  g.b_ns = 1;
+  g.b_ks = m;
   if (I == 1) {
-    const long long R = O;
-    const long long rows_per_z = 65535LL * TM;
-    for (long long rlo = 0; rlo < R; rlo += rows_per_z) {
-      const int Rz = (int)std::min(rows_per_z, R - rlo);
-      dim3 grid((m + TN - 1) / TN, (Rz + TM - 1) / TM, 1);
-      fd_tc_kernel<float><<<grid, 128, smem, s>>>(Rz, m, m, in + rlo * m, m, 1, 0, G, m, 1, 0,
-                                                  out + rlo * m, m, 1, 0, sc, g_tc_err);
-      count_launch();
-    }
+    // last axis: out[r][n] = sum_k in[r][k] G[k][n], rows R = data rows
+    g.M = (int)O;
+    g.Ia = INT_MAX;
+    g.A = in;
+    g.a_zs = 0;
+    g.a_rs = m;
+    g.a_ks = 1;
+    g.C = out;
+    g.c_zs = 0;
+    g.c_rs = m;
+    g.c_ns = 1;
   } else {
-    const long long zmax = 65535;
-    for (long long o0 = 0; o0 < O; o0 += zmax) {
-      const int nz = (int)std::min(zmax, O - o0);
-      dim3 grid((unsigned)((I + TN - 1) / TN), (m + TM - 1) / TM, nz);
-      fd_tc_kernel<float><<<grid, 128, smem, s>>>(m, (int)I, m, G, 1, m, 0, in + o0 * m * I, I, 1,
-                                                  (long long)m * I, out + o0 * m * I, I, 1,
-                                                  (long long)m * I, sc, g_tc_err);
-      count_launch();
-    }
+    // out[o][n][c] = sum_k G[k][n] in[o][k][c], rows R = (o, c), c at unit stride
+    g.M = (int)(O * I);
+    g.Ia = (int)I;
+    g.A = in;
+    g.a_zs = (long long)m * I;
+    g.a_rs = 1;
+    g.a_ks = I;
+    g.C = out;
+    g.c_zs = (long long)m * I;
+    g.c_rs = 1;
+    g.c_ns = I;
   }
+  const size_t smem = std::max((size_t)NST * (A_BYTES + tn * KC * 4), (size_t)EPI_BYTES);
+  dim3 grid((unsigned)((g.M + TM - 1) / TM), (unsigned)((m + tn - 1) / tn), 1);
+  fd_tc_kernel<<<grid, NTHR, smem, s>>>(g, sc, g_tc_err);
+  count_launch();
   return true;
 }
 

@@ -1122,6 +1122,8 @@ static int tuned_variant(size_t es, int m, int P, int /*B*/) {
 }
 static int g_use_v2 = 2;  // 2: v3 kernel, 1: v2 kernel, 0: v1 kernel
 void set_apply_variant(int v) { g_use_v2 = v; }
+static int g_fp64_v3 = 0;  // FP64 2D apply: 0 = v2 (default), 1 = v3 (8 rows per tile)
+void set_apply_fp64_variant(int v) { g_fp64_v3 = v; }
 void set_apply3d_variant(int v) { g_use_stream3d = v; }
 
 int prepare_kernels() {
@@ -1170,6 +1172,9 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
     g_epi<T> = Epi<T>{};
   }
   if (d == 2) {
+    if (sizeof(T) == 8 && g_use_v2 == 2 && g_fp64_v3 &&
+        try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, 8))
+      return 0;
     int tuned = g_use_v2 == 2 ? tuned_variant(sizeof(T), m, P, B) : 0;
     if (tuned == 1 && try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, 16))
       return 0;

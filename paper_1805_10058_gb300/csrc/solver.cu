@@ -690,6 +690,8 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     const char* v = std::getenv("CURLDIV_APPLY_KERNEL");
     const std::string vs = v ? v : "";
     set_apply_variant(vs == "v1" ? 0 : vs == "v2" ? 1 : 2);
+    const char* v64 = std::getenv("CURLDIV_APPLY_KERNEL_FP64");
+    set_apply_fp64_variant(v64 && std::string(v64) == "v3" ? 1 : 0);
     const char* v3d = std::getenv("CURLDIV_APPLY3D_KERNEL");
     set_apply3d_variant(v3d && std::string(v3d) == "multipass" ? 0 : 1);
   }

@@ -46,6 +46,7 @@ def test_apply_fp64_and_fp32_match_oracle(d, p, n, variant, monkeypatch):
         monkeypatch.setenv("CURLDIV_APPLY3D_KERNEL", "stream" if variant == "v3" else "multipass")
     else:
         monkeypatch.setenv("CURLDIV_APPLY_KERNEL", variant)
+        monkeypatch.setenv("CURLDIV_APPLY_KERNEL_FP64", "v3" if variant == "v3" else "v2")
     alphas = np.array([1.0, 0.5, 3.0])
     betas = np.array([0.1, 7.0, 3.0])
     s = cdl.Solver(d, p, n, max_batch=3)
