@@ -255,6 +255,9 @@ __global__ void __launch_bounds__(NTHR, 1) fd_tc_kernel(FdTcArgs g, FdScale<floa
       }
       if (sc.mode == 1) coef0 = comp == 0 ? sc.beta[bsol] : sc.alpha[bsol];
     }
+    // the transform is TF32: the per-element step of the scaling is FP32 (the row's part, a
+    // sum of up to d - 1 products, was formed in FP64)
+    const float srowf = (float)srow, coef0f = (float)coef0;
 #pragma unroll 1
     for (int cb = 8 * half; cb < ncol; cb += 16) {
       uint32_t v[8];
@@ -271,9 +274,8 @@ __global__ void __launch_bounds__(NTHR, 1) fd_tc_kernel(FdTcArgs g, FdScale<floa
           const int n = c0 + cb + j;
           float out = __uint_as_float(v[j]);
           if (sc.mode) {
-            const double lam0 = (double)sc.lam[n];
-            const double den = sc.mode == 1 ? srow + coef0 * lam0 : srow * lam0;
-            out = (float)((double)out / den);
+            const float lam0 = sc.lam[n];
+            out = __fdividef(out, sc.mode == 1 ? fmaf(coef0f, lam0, srowf) : srowf * lam0);
           }
           crow[(long long)n * g.c_ns] = out;
         }
