@@ -86,6 +86,23 @@ __device__ __forceinline__ double inv_diag2(double x, double y, double z, double
   return __ddiv_rn(1.0, __dadd_rn(__dmul_rn(__dmul_rn(x, y), z), __dmul_rn(__dmul_rn(u, v), t)));
 }
 
+// 1 / (diagonal entry of block c of the 3D operator) at a grid point whose 1D mass and
+// stiffness diagonals along the three axes are Md, Sd:
+//   sum_l (l == c ? beta : alpha) prod_k (k == l ? Sd[k] : Md[k]),
+// in the kernel's arithmetic type (FP32 kernels stay off the FP64 pipe).
+template <typename T>
+__device__ __forceinline__ T inv_diag3(T al, T be, int c, const T* Md, const T* Sd) {
+  T diag = T(0);
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    T t = (l == c) ? be : al;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t *= (k == l) ? Sd[k] : Md[k];
+    diag += t;
+  }
+  return T(1) / diag;
+}
+
 // ------------------------------------------------------------------ 2D fused apply
 // One CTA: TR output rows (axis x_1) of one solve, all m columns (axis x_2), both
 // components.  Shared memory: bands [3][m][W], input rows [2][TR+2P][m] (zero outside
@@ -946,20 +963,21 @@ __global__ void __launch_bounds__(32 * T2, 2) apply3d_stream_kernel(
       const int kd = q - P;
       const int slot = ((s - P) % W + W) % W;
       if (kd >= k_lo && kd < k_hi && mine) {
+        T Md[3], Sd[3];
+        if (mode == 2) {
+          const int I[3] = {kd, i2, i3};
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            Md[kx] = BX[0][(size_t)P * m + I[kx]];
+            Sd[kx] = BX[2][(size_t)P * m + I[kx]];
+          }
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const long long o = (long long)b * N + (long long)c * n3 + ((long long)kd * m + i2) * m + i3;
           const T v = acc[slot][c];
           if (mode == 2) {
-            const int I[3] = {kd, i2, i3};
-            double diag = 0.0;
-            for (int l = 0; l < 3; ++l) {
-              double tt = (l == c) ? (double)be : (double)al;
-              for (int kx = 0; kx < 3; ++kx)
-                tt *= (double)((kx == l) ? BX[2][(size_t)P * m + I[kx]] : BX[0][(size_t)P * m + I[kx]]);
-              diag += tt;
-            }
-            cheb_epi(epi, o, rhs[o] - v, T(1.0 / diag), ec1, ec2);
+            cheb_epi(epi, o, rhs[o] - v, inv_diag3(al, be, c, Md, Sd), ec1, ec2);
           } else if (mode == 1) {
             const T r = rhs[o] - v;
             y[o] = r;
@@ -1070,14 +1088,14 @@ __global__ void __launch_bounds__(256) post3d_kernel(long long N, const T* __res
       long long rem = i - comp * n3;
       const int i2 = (int)(rem % m), i1 = (int)((rem / m) % m), i0 = (int)(rem / ((long long)m * m));
       const int I[3] = {i0, i1, i2};
-      double diag = 0.0;
-      for (int l = 0; l < 3; ++l) {
-        double t = (l == comp) ? beta[b] : alpha[b];
-        for (int k = 0; k < 3; ++k)
-          t *= (double)((k == l) ? bands[(size_t)2 * m * W + I[k] * W + P] : bands[(size_t)I[k] * W + P]);
-        diag += t;
+      T Md[3], Sd[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        Md[k] = bands[(size_t)I[k] * W + P];
+        Sd[k] = bands[(size_t)2 * m * W + I[k] * W + P];
       }
-      cheb_epi(epi, base + i, rhs[base + i] - v, T(1.0 / diag), ec1, ec2);
+      cheb_epi(epi, base + i, rhs[base + i] - v, inv_diag3(T(alpha[b]), T(beta[b]), comp, Md, Sd),
+               ec1, ec2);
       continue;
     }
     if (mode == 1) {
