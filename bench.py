@@ -108,6 +108,18 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate(total_ms, solves_local, ws, device=None):
+    """Whole-job throughput over ws ranks: every rank's solves over the slowest rank's time
+    (all_reduce MAX of the timed milliseconds).  Returns (max_ms, solves per second)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, ws * solves_local / (total_ms / 1e3)
+
+
 # ------------------------------------------------------------------ reference (oracle) arm
 # The oracle's sparse direct solve takes minutes per n = 256 system and its CG needs
 # 10^4+ iterations below beta = 1e-3, so the CPU arm times a bounded sample: the paper's
@@ -226,20 +238,25 @@ def run_ours(args):
     for _ in range(args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        # device time of the step: the solver streams start after ev0 and ev1 follows all of them
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for st in streams:
+            st.wait_event(ev0)
         lat_all.extend(step(recs))
+        for st in streams:
+            e = torch.cuda.Event()
+            e.record(st)
+            stream.wait_event(e)
+        ev1.record(stream)
         torch.cuda.synchronize()
-        ms = 1e3 * (time.perf_counter() - t0)
+        ms = ev0.elapsed_time(ev1)
         step_ms.append(ms)
         total_ms += ms
     launches = cdl.cd_kernel_launches() - launches0
     clk = clocks.stop()
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     n_solves = len(PS) * B * args.steps
-    value = ws * n_solves / (total_ms / 1e3)
+    total_ms, value = aggregate(total_ms, n_solves, ws, device=dev)
     flat = [r for step_res in recs for r in step_res]
     ok = sum(1 for r in flat if r["status"] == 0)
     worst = max(r["relres"] for r in flat)
