@@ -832,11 +832,12 @@ static int apply3d_multipass(int m, int P, const T* bands, const T* w, T* y, int
 // it stages the haloed tile of w (3 components) in shared memory, applies the x_3 operators
 // (9 arrays T_{X,c} = X_3 w_c on the tile plus P halo rows of x_2), then each thread forms its
 // point's 9 x_2-results (grouped by the x_1 operator they feed, as in the multi-pass version)
-// and scatters them into a ring of 2P+1 pending output planes:
+// and scatters them into 2P+1 pending output planes held as a register shift register:
 //   y_c[k] += M_1(k,q) P_cM[q] + S_1(k,q) P_cS[q] + A_1(k,q) P_cA[q],  |k - q| <= P.
 // Plane k is complete once q = k + P has been handled (or the last plane, near the end of the
-// domain); it then leaves through the epilogue (modes 0, 1, 2) and its slot is cleared.  The
-// slot of plane k is k mod (2P+1): a compile-time index in the plane loop unrolled by 2P+1.
+// domain); it then leaves through the epilogue (modes 0, 1, 2) and the planes shift by one (one
+// loop body for every plane).  The next plane's tile is loaded into registers while the
+// current one is computed.
 // Central Toeplitz stencils come from the constant bank, boundary rows from bandT.
 template <typename T>
 __device__ __forceinline__ T band_coef(const Stencil<T>& cs, const T* const* BX, int m, int X,
@@ -874,123 +875,139 @@ __global__ void __launch_bounds__(32 * T2, 2) apply3d_stream_kernel(
     ec1 = T(c1);
     ec2 = T(c2);
   }
-  T acc[W][3];
+  T acc[W][3];  // acc[t]: pending output plane q - P + t (a shift register over the planes)
 #pragma unroll
   for (int sl = 0; sl < W; ++sl) acc[sl][0] = acc[sl][1] = acc[sl][2] = T(0);
   double dacc = 0.0;
   const int q_begin = max(0, k_lo - P), q_end = min(m, k_hi + P);
-  for (int qb = (q_begin / W) * W; qb < q_end + P; qb += W) {
+  // the next plane's haloed tile, loaded into registers while the current one is computed
+  constexpr int NE = (3 * HR * HC + 32 * T2 - 1) / (32 * T2);
+  T pre[NE];
+  auto load_plane = [&](int q) {
 #pragma unroll
-    for (int s = 0; s < W; ++s) {
-      const int q = qb + s;
-      if (q >= q_begin && q < q_end) {  // uniform over the CTA
-        __syncthreads();
-        for (int e = threadIdx.x; e < 3 * HR * HC; e += blockDim.x) {
-          const int c = e / (HR * HC), rem = e - c * HR * HC;
-          const int rr = rem / HC, cc = rem - rr * HC;
-          const int g2 = i2_0 - P + rr, g3 = i3_0 - P + cc;
-          sw[e] = (g2 >= 0 && g2 < m && g3 >= 0 && g3 < m)
-                      ? wb[(long long)c * n3 + ((long long)q * m + g2) * m + g3]
-                      : T(0);
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < HR * T3; e += blockDim.x) {  // x_3 operators
-          const int rr = e / T3, cc = e - rr * T3;
-          const int g3 = i3_0 + cc;
-          T t[9];
+    for (int t = 0; t < NE; ++t) {
+      const int e = threadIdx.x + t * 32 * T2;
+      if (e < 3 * HR * HC) {
+        const int c = e / (HR * HC), rem = e - c * HR * HC;
+        const int rr = rem / HC, cc = rem - rr * HC;
+        const int g2 = i2_0 - P + rr, g3 = i3_0 - P + cc;
+        pre[t] = (g2 >= 0 && g2 < m && g3 >= 0 && g3 < m)
+                     ? wb[(long long)c * n3 + ((long long)q * m + g2) * m + g3]
+                     : T(0);
+      }
+    }
+  };
+  if (q_begin < q_end) load_plane(q_begin);
+#pragma unroll 1
+  for (int q = q_begin; q < q_end + P; ++q) {
+    if (q < q_end) {  // uniform over the CTA
+      __syncthreads();
 #pragma unroll
-          for (int u = 0; u < 9; ++u) t[u] = T(0);
-          if (g3 < m) {
+      for (int t = 0; t < NE; ++t) {
+        const int e = threadIdx.x + t * 32 * T2;
+        if (e < 3 * HR * HC) sw[e] = pre[t];
+      }
+      if (q + 1 < q_end) load_plane(q + 1);
+      __syncthreads();
+      for (int e = threadIdx.x; e < HR * T3; e += blockDim.x) {  // x_3 operators
+        const int rr = e / T3, cc = e - rr * T3;
+        const int g3 = i3_0 + cc;
+        T t[9];
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-              const T cM = band_coef(cs, BX, m, 0, g3, k), cA = band_coef(cs, BX, m, 1, g3, k),
-                      cS = band_coef(cs, BX, m, 2, g3, k);
-#pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                const T v = sw[(c * HR + rr) * HC + cc + k];
-                t[0 * 3 + c] += cM * v;
-                t[1 * 3 + c] += cA * v;
-                t[2 * 3 + c] += cS * v;
-              }
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 9; ++u) st[(u * HR + rr) * T3 + cc] = t[u];
-        }
-        __syncthreads();
-        T PM[3], PS[3], PA[3];  // x_2 results of this point, grouped by the x_1 operator
-#pragma unroll
-        for (int c = 0; c < 3; ++c) PM[c] = PS[c] = PA[c] = T(0);
-        if (mine) {
+        for (int u = 0; u < 9; ++u) t[u] = T(0);
+        if (g3 < m) {
 #pragma unroll
           for (int k = 0; k < W; ++k) {
-            const T cM = band_coef(cs, BX, m, 0, i2, k), cA = band_coef(cs, BX, m, 1, i2, k),
-                    cS = band_coef(cs, BX, m, 2, i2, k);
-            const int rr = row + k;
-            const T tM1 = st[(0 * HR + rr) * T3 + lane], tM2 = st[(1 * HR + rr) * T3 + lane];
-            const T tM3 = st[(2 * HR + rr) * T3 + lane], tA1 = st[(3 * HR + rr) * T3 + lane];
-            const T tA2 = st[(4 * HR + rr) * T3 + lane], tA3 = st[(5 * HR + rr) * T3 + lane];
-            const T tS1 = st[(6 * HR + rr) * T3 + lane], tS2 = st[(7 * HR + rr) * T3 + lane];
-            const T tS3 = st[(8 * HR + rr) * T3 + lane];
-            // component 1: M1[alpha (M2 S3 + S2 M3) w1], S1[beta M2 M3 w1], A1[gamma (A2 M3 w2 + M2 A3 w3)]
-            PM[0] += al * (cM * tS1 + cS * tM1);
-            PS[0] += be * (cM * tM1);
-            PA[0] += ga * (cA * tM2 + cM * tA3);
-            // component 2: S1[alpha M2 M3 w2], M1[alpha M2 S3 w2 + beta S2 M3 w2 + gamma A2 A3 w3], A1[gamma A2 M3 w1]
-            PS[1] += al * (cM * tM2);
-            PM[1] += al * (cM * tS2) + be * (cS * tM2) + ga * (cA * tA3);
-            PA[1] += ga * (cA * tM1);
-            // component 3: S1[alpha M2 M3 w3], M1[alpha S2 M3 w3 + beta M2 S3 w3 + gamma A2 A3 w2], A1[gamma M2 A3 w1]
-            PS[2] += al * (cM * tM3);
-            PM[2] += al * (cS * tM3) + be * (cM * tS3) + ga * (cA * tA2);
-            PA[2] += ga * (cM * tA1);
+            const T cM = band_coef(cs, BX, m, 0, g3, k), cA = band_coef(cs, BX, m, 1, g3, k),
+                    cS = band_coef(cs, BX, m, 2, g3, k);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              const T v = sw[(c * HR + rr) * HC + cc + k];
+              t[0 * 3 + c] += cM * v;
+              t[1 * 3 + c] += cA * v;
+              t[2 * 3 + c] += cS * v;
+            }
           }
         }
 #pragma unroll
-        for (int dd = 0; dd < W; ++dd) {  // x_1 scatter: plane kk = q - (dd - P), column dd
-          const int kk = q - (dd - P);
-          if (kk >= k_lo && kk < k_hi) {
-            constexpr int WW = W;
-            const int slot = ((s - (dd - P)) % WW + WW) % WW;
-            const T cM = band_coef(cs, BX, m, 0, kk, dd), cA = band_coef(cs, BX, m, 1, kk, dd),
-                    cS = band_coef(cs, BX, m, 2, kk, dd);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) acc[slot][c] += cM * PM[c] + cS * PS[c] + cA * PA[c];
-          }
-        }
+        for (int u = 0; u < 9; ++u) st[(u * HR + rr) * T3 + cc] = t[u];
       }
-      // plane kd = q - P has received every contribution (q = kd + P, or the last plane m - 1)
-      const int kd = q - P;
-      const int slot = ((s - P) % W + W) % W;
-      if (kd >= k_lo && kd < k_hi && mine) {
-        T Md[3], Sd[3];
-        if (mode == 2) {
-          const int I[3] = {kd, i2, i3};
+      __syncthreads();
+      T PM[3], PS[3], PA[3];  // x_2 results of this point, grouped by the x_1 operator
 #pragma unroll
-          for (int kx = 0; kx < 3; ++kx) {
-            Md[kx] = BX[0][(size_t)P * m + I[kx]];
-            Sd[kx] = BX[2][(size_t)P * m + I[kx]];
-          }
-        }
+      for (int c = 0; c < 3; ++c) PM[c] = PS[c] = PA[c] = T(0);
+      if (mine) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const long long o = (long long)b * N + (long long)c * n3 + ((long long)kd * m + i2) * m + i3;
-          const T v = acc[slot][c];
-          if (mode == 2) {
-            cheb_epi(epi, o, rhs[o] - v, inv_diag3(al, be, c, Md, Sd), ec1, ec2);
-          } else if (mode == 1) {
-            const T r = rhs[o] - v;
-            y[o] = r;
-            dacc += (double)r * (double)r;
-          } else {
-            y[o] = v;
-            if (dotp) dacc += (double)w[o] * (double)v;
-          }
+        for (int k = 0; k < W; ++k) {
+          const T cM = band_coef(cs, BX, m, 0, i2, k), cA = band_coef(cs, BX, m, 1, i2, k),
+                  cS = band_coef(cs, BX, m, 2, i2, k);
+          const int rr = row + k;
+          const T tM1 = st[(0 * HR + rr) * T3 + lane], tM2 = st[(1 * HR + rr) * T3 + lane];
+          const T tM3 = st[(2 * HR + rr) * T3 + lane], tA1 = st[(3 * HR + rr) * T3 + lane];
+          const T tA2 = st[(4 * HR + rr) * T3 + lane], tA3 = st[(5 * HR + rr) * T3 + lane];
+          const T tS1 = st[(6 * HR + rr) * T3 + lane], tS2 = st[(7 * HR + rr) * T3 + lane];
+          const T tS3 = st[(8 * HR + rr) * T3 + lane];
+          // component 1: M1[alpha (M2 S3 + S2 M3) w1], S1[beta M2 M3 w1], A1[gamma (A2 M3 w2 + M2 A3 w3)]
+          PM[0] += al * (cM * tS1 + cS * tM1);
+          PS[0] += be * (cM * tM1);
+          PA[0] += ga * (cA * tM2 + cM * tA3);
+          // component 2: S1[alpha M2 M3 w2], M1[alpha M2 S3 w2 + beta S2 M3 w2 + gamma A2 A3 w3], A1[gamma A2 M3 w1]
+          PS[1] += al * (cM * tM2);
+          PM[1] += al * (cM * tS2) + be * (cS * tM2) + ga * (cA * tA3);
+          PA[1] += ga * (cA * tM1);
+          // component 3: S1[alpha M2 M3 w3], M1[alpha S2 M3 w3 + beta M2 S3 w3 + gamma A2 A3 w2], A1[gamma M2 A3 w1]
+          PS[2] += al * (cM * tM3);
+          PM[2] += al * (cS * tM3) + be * (cM * tS3) + ga * (cA * tA2);
+          PA[2] += ga * (cM * tA1);
         }
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[slot][c] = T(0);
+      for (int dd = 0; dd < W; ++dd) {  // x_1 scatter: plane kk = q - (dd - P) is slot 2P - dd
+        const int kk = q - (dd - P);
+        if (kk >= k_lo && kk < k_hi) {
+          const T cM = band_coef(cs, BX, m, 0, kk, dd), cA = band_coef(cs, BX, m, 1, kk, dd),
+                  cS = band_coef(cs, BX, m, 2, kk, dd);
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            acc[2 * P - dd][c] += cM * PM[c] + cS * PS[c] + cA * PA[c];
+        }
+      }
     }
+    // plane kd = q - P (slot 0) has received every contribution (q = kd + P, or the last plane)
+    const int kd = q - P;
+    if (kd >= k_lo && kd < k_hi && mine) {
+      T Md[3], Sd[3];
+      if (mode == 2) {
+        const int I[3] = {kd, i2, i3};
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          Md[kx] = BX[0][(size_t)P * m + I[kx]];
+          Sd[kx] = BX[2][(size_t)P * m + I[kx]];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const long long o = (long long)b * N + (long long)c * n3 + ((long long)kd * m + i2) * m + i3;
+        const T v = acc[0][c];
+        if (mode == 2) {
+          cheb_epi(epi, o, rhs[o] - v, inv_diag3(al, be, c, Md, Sd), ec1, ec2);
+        } else if (mode == 1) {
+          const T r = rhs[o] - v;
+          y[o] = r;
+          dacc += (double)r * (double)r;
+        } else {
+          y[o] = v;
+          if (dotp) dacc += (double)w[o] * (double)v;
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 2 * P; ++t) {
+      acc[t][0] = acc[t + 1][0];
+      acc[t][1] = acc[t + 1][1];
+      acc[t][2] = acc[t + 1][2];
+    }
+    acc[2 * P][0] = acc[2 * P][1] = acc[2 * P][2] = T(0);
   }
   if (dotp && mode != 2) {
     const double sum = block_sum(dacc);
