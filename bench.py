@@ -442,6 +442,30 @@ def run_serving(args):
     return 0
 
 
+def run_profile_kernel(args):
+    """A few launches of one kernel on its profiling case, for ncu (no timing): `apply` = the
+    FP32 2D apply at p = 3, n = 256, batch 40 (four calls); `fd` = two FP32 FD-D applications
+    on the tensor cores at the same size (four passes each)."""
+    import torch
+    from paper_1805_10058_gb300 import curldiv as cdl
+    B = 40
+    if args.profile_kernel == "apply":
+        s = cdl.Solver(2, 3, N_INT, max_batch=B, precond=cdl.CD_PC_NONE)
+        w = torch.rand(B * s.N, dtype=torch.float32, device="cuda")
+        y = torch.empty_like(w)
+        for _ in range(4):
+            s.cd_apply_f32(w, y, [1.0] * B, [1e-3] * B)
+    else:
+        s = cdl.Solver(2, 3, N_INT, max_batch=B, precond=cdl.CD_PC_FD_D, fd_tensor_cores=1)
+        r = torch.rand(B * s.N, dtype=torch.float32, device="cuda")
+        z = torch.empty_like(r)
+        for _ in range(2):
+            s.cd_precond(cdl.CD_PC_FD_D, r, z, [1.0] * B, [1e-3] * B)
+    torch.cuda.synchronize()
+    print("ok")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -455,7 +479,11 @@ def main():
     ap.add_argument("--serving", action="store_true", help="serving-stream workload instead")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--profile-kernel", choices=["apply", "fd"], default=None,
+                    help="a few launches of one kernel for ncu, no timing")
     args = ap.parse_args()
+    if args.profile_kernel:
+        return run_profile_kernel(args)
     if args.serving:
         return run_serving(args)
     if args.impl == "reference":
