@@ -81,8 +81,11 @@ enum { CD_PREC_FP64 = 0, CD_PREC_FP32_IR = 1 };
  *   by fast diagonalisation of the 1D factor.
  * CD_PC_MG: one V-cycle of the Galerkin multigrid of Section 6.1 (block
  *   prolongator eq:2by2prol, R = P^T, A_{l+1} = P^T A_l P) with a parallel
- *   smoother; the outer Krylov method is then flexible CG. */
-enum { CD_PC_NONE = 0, CD_PC_FD_D = 1, CD_PC_FD_T = 2, CD_PC_MG = 3 };
+ *   smoother; the outer Krylov method is then flexible CG.
+ * CD_PC_T_BAND: the same T^{-1} as CD_PC_FD_T, by banded Cholesky solves of the
+ *   1D factor along every axis (Section 6.1 applies T by banded factorisation):
+ *   O(N p) work per application instead of O(N m); p <= 6. */
+enum { CD_PC_NONE = 0, CD_PC_FD_D = 1, CD_PC_FD_T = 2, CD_PC_MG = 3, CD_PC_T_BAND = 4 };
 
 typedef struct {
   int precision;      /* CD_PREC_*                      (default CD_PREC_FP32_IR) */
@@ -157,8 +160,9 @@ CD_API cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host
                                cd_result* res);
 
 /* One application z = B^{-1} r of a preconditioner kind (CD_PC_FD_D: D^{-1},
- * eq:diag; CD_PC_FD_T: T^{-1}, eq:kron_precond; CD_PC_MG: one V-cycle from
- * zero) in FP64 (`f32` = 0) or FP32 (`f32` = 1, pointers then hold floats).
+ * eq:diag; CD_PC_FD_T and CD_PC_T_BAND: T^{-1}, eq:kron_precond; CD_PC_MG: one
+ * V-cycle from zero) in FP64 (`f32` = 0) or FP32 (`f32` = 1, pointers then hold
+ * floats).
  * Device pointers.  CD_EINVAL if the handle was created without the data the
  * kind needs (FD kinds need an FD preconditioner or CD_PC_MG needs... see
  * cd_create: every handle builds all three). */

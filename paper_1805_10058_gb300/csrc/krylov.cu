@@ -563,6 +563,78 @@ void to_f64(long long N, int B, const float* src, double* dst, const int* active
   count_launch();
 }
 
+// ------------------------------------------------------------------ banded T solves
+// One thread per pencil (a line of m values along the axis, at stride I): forward substitution
+// with L, then backward substitution with L^T, each keeping the last q values in registers.
+// Pencil (o, c): first value at o * m * I + c; consecutive threads take consecutive c, so the
+// accesses of a warp are contiguous for every axis but the last.
+template <typename T, int Q>
+__global__ void __launch_bounds__(256) tband_kernel(int m, long long I, long long npencil,
+                                                    long long opb, const T* __restrict__ Lb,
+                                                    const T* __restrict__ dinv, const T* in,
+                                                    T* out, const int* __restrict__ active) {
+  const long long pid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pid >= npencil) return;
+  const long long o = pid / I, c = pid - o * I;
+  if (active && !active[o / opb]) return;
+  const T* x = in + o * m * I + c;
+  T* y = out + o * m * I + c;
+  T win[Q + 1];  // forward: win[t] = y_{i - Q + t}; backward: win[u] = x_{i + 1 + u}
+#pragma unroll
+  for (int t = 0; t <= Q; ++t) win[t] = T(0);
+  for (int i = 0; i < m; ++i) {
+    T v = x[(long long)i * I];
+#pragma unroll
+    for (int t = 0; t < Q; ++t) v -= Lb[(size_t)i * Q + t] * win[t];
+    v *= dinv[i];
+    y[(long long)i * I] = v;
+#pragma unroll
+    for (int t = 0; t + 1 < Q; ++t) win[t] = win[t + 1];
+    if (Q > 0) win[Q - 1] = v;
+  }
+#pragma unroll
+  for (int t = 0; t <= Q; ++t) win[t] = T(0);
+  for (int i = m - 1; i >= 0; --i) {
+    T v = y[(long long)i * I];
+    // (L^T x)_i = sum_{u=0..Q} L(i + u, i) x_{i+u}, L(i + u, i) = Lb[(i + u) * Q + Q - u]
+#pragma unroll
+    for (int u = 1; u <= Q; ++u) v -= Lb[(size_t)(i + u) * Q + (Q - u)] * win[u - 1];
+    v *= dinv[i];
+    y[(long long)i * I] = v;
+#pragma unroll
+    for (int u = Q - 1; u > 0; --u) win[u] = win[u - 1];
+    if (Q > 0) win[0] = v;
+  }
+}
+
+template <typename T>
+int launch_tband(int d, int m, int q, int B, const T* Lb, const T* dinv, const T* in, T* out,
+                 const int* active, cudaStream_t s) {
+  if (q < 0 || q > 5) return 1;
+  for (int a = 0; a < d; ++a) {
+    long long I = 1, opb = d;
+    for (int l = a + 1; l < d; ++l) I *= m;
+    for (int l = 0; l < a; ++l) opb *= m;
+    const long long np = (long long)B * opb * I;
+    const unsigned grid = (unsigned)((np + 255) / 256);
+    const T* src = a == 0 ? in : out;
+    switch (q) {
+      case 0: tband_kernel<T, 0><<<grid, 256, 0, s>>>(m, I, np, opb, Lb, dinv, src, out, active); break;
+      case 1: tband_kernel<T, 1><<<grid, 256, 0, s>>>(m, I, np, opb, Lb, dinv, src, out, active); break;
+      case 2: tband_kernel<T, 2><<<grid, 256, 0, s>>>(m, I, np, opb, Lb, dinv, src, out, active); break;
+      case 3: tband_kernel<T, 3><<<grid, 256, 0, s>>>(m, I, np, opb, Lb, dinv, src, out, active); break;
+      case 4: tband_kernel<T, 4><<<grid, 256, 0, s>>>(m, I, np, opb, Lb, dinv, src, out, active); break;
+      default: tband_kernel<T, 5><<<grid, 256, 0, s>>>(m, I, np, opb, Lb, dinv, src, out, active); break;
+    }
+    count_launch();
+  }
+  return 0;
+}
+template int launch_tband<double>(int, int, int, int, const double*, const double*, const double*,
+                                  double*, const int*, cudaStream_t);
+template int launch_tband<float>(int, int, int, int, const float*, const float*, const float*,
+                                 float*, const int*, cudaStream_t);
+
 template void vcopy<double>(long long, int, const double*, double*, const int*, cudaStream_t);
 template void vcopy<float>(long long, int, const float*, float*, const int*, cudaStream_t);
 template void vzero<double>(long long, int, double*, const int*, cudaStream_t);

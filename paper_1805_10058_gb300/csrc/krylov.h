@@ -35,6 +35,14 @@ template <typename T>
 int launch_fd_axis(int d, int m, int axis, int B, const T* G, const T* in, T* out,
                    FdScale<T> sc, const int* active, cudaStream_t s);
 
+// z = T^{-1} r with T = I_d (x) T_m (x) ... (eq:kron_precond) by banded Cholesky solves along
+// every axis (the banded factorisation route of Section 6.1).  T_m = L L^T with L lower banded
+// of half-bandwidth q = p - 1: Lb[i * q + t] = L(i, i - q + t) for t < q ((m + q) x q, rows
+// past m and entries left of column 0 zero), dinv[i] = 1 / L(i, i).  in == out is allowed.
+template <typename T>
+int launch_tband(int d, int m, int q, int B, const T* Lb, const T* dinv, const T* in, T* out,
+                 const int* active, cudaStream_t s);
+
 // tcgen05 (TF32) version of launch_fd_axis<float>; fd_tc_error() reports a bounded wait that
 // expired inside the kernel (then its output is not written).
 bool launch_fd_axis_tc(int d, int m, int axis, int B, const float* G, const float* in, float* out,

@@ -78,6 +78,9 @@ struct cd_solver_s {
   std::vector<double> UD, lamD, UT, lamT;
   DevBuf UD64, UDt64, lamD64, UT64, UTt64, lamT64, UD32, UDt32, lamD32, UT32, UTt32, lamT32;
   bool have_fd = false;
+  // banded Cholesky factor of T_m (off-diagonal taps, inverse diagonal), built on first need
+  DevBuf TB64, TBd64, TB32, TBd32;
+  bool have_tband = false;
   // per-solve coefficients and state
   DevBuf alpha, beta;
   DevBuf sd[6];  // rz rr rr0 alpha beta rzold
@@ -163,6 +166,12 @@ static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* 
     mg_vcycle<T>(h->mg, h->d, h->P, B, r, z, coef_of(h), active, h->s, w.apply_scratch.as<T>());
     return;
   }
+  if (pc == CD_PC_T_BAND) {
+    const T* Lb = (const T*)(sizeof(T) == 8 ? h->TB64.p : h->TB32.p);
+    const T* dinv = (const T*)(sizeof(T) == 8 ? h->TBd64.p : h->TBd32.p);
+    launch_tband<T>(h->d, h->m, h->p - 1, B, Lb, dinv, r, z, active, h->s);
+    return;
+  }
   const bool isD = pc == CD_PC_FD_D;
   const T *U, *Ut, *lam;
   if (sizeof(T) == 8) {
@@ -237,7 +246,10 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
   // a Krylov-smoothed / multigrid or tensor-core (TF32) preconditioner is not an exactly
   // fixed symmetric operator: use the flexible update there
   const int flexible =
-      (pc == CD_PC_MG || (sizeof(T) == 4 && h->opt.fd_tensor_cores && pc != CD_PC_NONE)) ? 1 : 0;
+      (pc == CD_PC_MG ||
+       (sizeof(T) == 4 && h->opt.fd_tensor_cores && (pc == CD_PC_FD_D || pc == CD_PC_FD_T)))
+          ? 1
+          : 0;
   vzero<T>(N, B, w.x.as<T>(), outer_active, h->s);
   apply_prec<T>(h, pc, B, w.r.as<T>(), w.z.as<T>(), outer_active);
   launch_dot<T>(w.r.as<T>(), w.r.as<T>(), N, B, h->part[1].as<double>(), nb, outer_active, h->s);
@@ -579,6 +591,8 @@ const char* cd_strerror(cd_status s) {
 const char* cd_last_error(void) { return cd::last_error(); }
 uint64_t cd_kernel_launches(void) { return cd::launches(); }
 
+static cd_status ensure_tband(cd_solver h);
+
 cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double beta,
                     const cd_options* opt, void* stream) {
   if (!out) return CD_EINVAL;
@@ -602,7 +616,7 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   cd_default_options(&h->opt);
   if (opt) h->opt = *opt;
   if (h->opt.max_batch < 1 || h->opt.max_batch > 4096 || h->opt.chunk < 1 || h->opt.maxit < 1 ||
-      !(h->opt.rtol > 0) || h->opt.precond < 0 || h->opt.precond > 3 || h->opt.precision < 0 ||
+      !(h->opt.rtol > 0) || h->opt.precond < 0 || h->opt.precond > CD_PC_T_BAND || h->opt.precision < 0 ||
       h->opt.precision > 1) {
     set_error("invalid options");
     return CD_EINVAL;
@@ -697,6 +711,10 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   }
   if (h->opt.precond == CD_PC_FD_D || h->opt.precond == CD_PC_FD_T) {
     cd_status st = ensure_fd(h.get());
+    if (st != CD_OK) return st;
+  }
+  if (h->opt.precond == CD_PC_T_BAND) {
+    cd_status st = ensure_tband(h.get());
     if (st != CD_OK) return st;
   }
   // workspace
@@ -832,14 +850,63 @@ cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int n
   return st;
 }
 
+// Banded Cholesky factor of T_m(m_{p-1}) (SPD: its eigenvalues lie in [(2/pi)^{2(p-1)}, 1]),
+// half-bandwidth q = p - 1, in FP64 on the host; FP64 and FP32 copies on the device.
+static cd_status ensure_tband(cd_solver h) {
+  if (h->have_tband) return CD_OK;
+  const int m = h->m, q = h->p - 1, P = h->P, W = 2 * P + 1;
+  if (q > 5) {
+    set_error("banded T solve: p <= 6");
+    return CD_EINVAL;
+  }
+  Band T;
+  toeplitz_T_band(h->p, m, P, T);
+  auto Tij = [&](int i, int j) { return T.v[(size_t)i * W + (j - i + P)]; };
+  std::vector<double> L((size_t)m * (q + 1), 0.0);  // L[i][t] = L(i, i - q + t), t = q diagonal
+  auto Lij = [&](int i, int j) -> double& { return L[(size_t)i * (q + 1) + (j - i + q)]; };
+  for (int i = 0; i < m; ++i)
+    for (int j = std::max(0, i - q); j <= i; ++j) {
+      double s = Tij(i, j);
+      for (int k = std::max(0, i - q); k < j; ++k) s -= Lij(i, k) * Lij(j, k);
+      if (i == j) {
+        if (!(s > 0.0)) {
+          set_error("banded Cholesky of T failed (not positive definite)");
+          return CD_EINVAL;
+        }
+        Lij(i, i) = std::sqrt(s);
+      } else {
+        Lij(i, j) = s / Lij(j, j);
+      }
+    }
+  std::vector<double> Lb((size_t)(m + q) * q, 0.0), dinv(m);
+  for (int i = 0; i < m; ++i) {
+    for (int t = 0; t < q; ++t)
+      if (i - q + t >= 0) Lb[(size_t)i * q + t] = Lij(i, i - q + t);
+    dinv[i] = 1.0 / Lij(i, i);
+  }
+  if (Lb.empty()) Lb.push_back(0.0);
+  if (upload(h->TB64, Lb) != cudaSuccess || upload(h->TBd64, dinv) != cudaSuccess ||
+      upload(h->TB32, cast_vec<float>(Lb)) != cudaSuccess ||
+      upload(h->TBd32, cast_vec<float>(dinv)) != cudaSuccess) {
+    set_error("banded T factor upload failed");
+    return CD_ECUDA;
+  }
+  h->have_tband = true;
+  return CD_OK;
+}
+
 cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs, const double* alphas,
                      const double* betas, int f32) {
   cd_status st = check_call(h, r, z, nrhs);
   if (st != CD_OK) return st;
-  if (kind < CD_PC_NONE || kind > CD_PC_MG) return CD_EINVAL;
+  if (kind < CD_PC_NONE || kind > CD_PC_T_BAND) return CD_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
   if (kind == CD_PC_FD_D || kind == CD_PC_FD_T) {
     st = ensure_fd(h);
+    if (st != CD_OK) return st;
+  }
+  if (kind == CD_PC_T_BAND) {
+    st = ensure_tband(h);
     if (st != CD_OK) return st;
   }
   st = set_params(h, nrhs, alphas, betas, nullptr, nullptr, kind == CD_PC_MG);

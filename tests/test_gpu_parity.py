@@ -123,6 +123,29 @@ def test_2d_large_grid_beyond_fused_partials():
         assert est <= 3e-9, est
 
 
+@pytest.mark.parametrize("d,p,n", [(2, 1, 7), (2, 3, 19), (2, 6, 30), (3, 2, 9), (3, 4, 6)])
+def test_banded_T_solve_matches_oracle(d, p, n):
+    """CD_PC_T_BAND (banded Cholesky of T_m along every axis) against the oracle's T solve
+    (one LU of the 1D factor per axis, Section 6.1) and against the fast-diagonalisation
+    inverse of the same T."""
+    B = 2
+    s = cdl.Solver(d, p, n, max_batch=B, precond=cdl.CD_PC_NONE)
+    m = n + p - 2
+    r = np.random.default_rng(p).uniform(-1, 1, B * s.N)
+    ts = solvers.TSolver(d, p, m)
+    ref = np.concatenate([ts(r[k * s.N:(k + 1) * s.N]) for k in range(B)])
+    z = torch.zeros(B * s.N, dtype=torch.float64, device="cuda")
+    s.cd_precond(cdl.CD_PC_T_BAND, dev(r), z)
+    Z = host(z)
+    assert np.abs(Z - ref).max() <= 1e-12 * np.abs(ref).max()
+    z32 = torch.zeros(B * s.N, dtype=torch.float32, device="cuda")
+    s.cd_precond(cdl.CD_PC_T_BAND, dev(r, torch.float32), z32)
+    assert np.abs(host(z32) - ref).max() <= 1e-4 * np.abs(ref).max()
+    zf = torch.zeros(B * s.N, dtype=torch.float64, device="cuda")
+    s.cd_precond(cdl.CD_PC_FD_T, dev(r), zf)
+    assert np.abs(host(zf) - Z).max() <= 1e-10 * np.abs(ref).max()
+
+
 def test_bands_match_oracle_matrices():
     for p, n in [(1, 8), (2, 16), (3, 37), (5, 20)]:
         s = cdl.Solver(2, p, n, max_batch=1)
@@ -220,6 +243,8 @@ SOLVE_CASES = [
     (3, 2, 8, cdl.CD_PREC_FP32_IR, cdl.CD_PC_FD_D),
     (3, 3, 7, cdl.CD_PREC_FP64, cdl.CD_PC_MG),
     (3, 2, 9, cdl.CD_PREC_FP32_IR, cdl.CD_PC_MG),
+    (2, 3, 24, cdl.CD_PREC_FP64, cdl.CD_PC_T_BAND),
+    (3, 2, 8, cdl.CD_PREC_FP32_IR, cdl.CD_PC_T_BAND),
 ]
 
 
