@@ -176,6 +176,23 @@ CD_API cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int n
 CD_API cd_status cd_get_bands(cd_solver h, int level, double* M, double* A, double* S,
                               int* m_out, int* P_out);
 
+/* Host-only set-up queries (no handle, no GPU; the library's own FP64 host code).
+ * cd_setup_bands: the 1D bands of Section 3.2 for degree p on n intervals (Gauss-Legendre
+ *   quadrature, p + 1 points per interval, Dirichlet basis, m = n + p - 2), Galerkin-coarsened
+ *   `level` times with the 3-tap prolongator of Section 6.1 (P^T X P); layout as
+ *   cd_get_bands (before a handle replaces the interior rows by the central row).
+ * cd_setup_eig: as cd_get_eig for the finest grid of (p, n).
+ * cd_setup_tband: the banded Cholesky factor T_m(m_{p-1}) = L L^T (eq:kron_precond,
+ *   half-bandwidth q = p - 1) used by CD_PC_T_BAND: Lb[(m + q) * q] with
+ *   Lb[i*q + t] = L(i, i-q+t) (zero left of column 0 and in the q rows past m), and
+ *   dinv[m] = 1 / L(i, i).
+ * All three: CD_EINVAL unless 1 <= p <= 6, n >= 1, m >= 1 (and level within the grid
+ * hierarchy); caller-owned host output arrays, any of which may be NULL. */
+CD_API cd_status cd_setup_bands(int p, int n, int level, double* M, double* A, double* S,
+                                int* m_out, int* P_out);
+CD_API cd_status cd_setup_eig(int p, int n, int which, double* U, double* lam);
+CD_API cd_status cd_setup_tband(int p, int n, double* Lb, double* dinv);
+
 /* Number of multigrid levels of the handle. */
 CD_API int cd_levels(cd_solver h);
 

@@ -49,6 +49,10 @@ bool sym_eig(int m, const std::vector<double>& Adense, std::vector<double>& U,
 bool gen_eig(int m, const std::vector<double>& Mdense, const std::vector<double>& Sdense,
              std::vector<double>& U, std::vector<double>& lam);
 std::vector<double> band_to_dense(const Band& X);
+// Banded Cholesky T_m(m_{p-1}) = L L^T, half-bandwidth q = p - 1: Lb[i * q + t] = L(i, i-q+t)
+// for t < q ((m + q) x q, zero where the column is < 0 and in the q rows past m),
+// dinv[i] = 1 / L(i, i).  False if a pivot is not positive.
+bool tband_factor(int p, int m, std::vector<double>& Lb, std::vector<double>& dinv);
 // Cholesky inverse of a small dense SPD matrix (FP64); false if not SPD.
 bool spd_inverse(int n, std::vector<double>& a);
 

@@ -160,6 +160,33 @@ void toeplitz_T_band(int p, int m, int P, Band& T) {
     }
 }
 
+bool tband_factor(int p, int m, std::vector<double>& Lb, std::vector<double>& dinv) {
+  const int q = p - 1, P = p, W = 2 * P + 1;
+  Band T;
+  toeplitz_T_band(p, m, P, T);
+  std::vector<double> L((size_t)m * (q + 1), 0.0);  // L[i][t] = L(i, i - q + t), t = q diagonal
+  auto Lij = [&](int i, int j) -> double& { return L[(size_t)i * (q + 1) + (j - i + q)]; };
+  for (int i = 0; i < m; ++i)
+    for (int j = std::max(0, i - q); j <= i; ++j) {
+      double s = T.v[(size_t)i * W + (j - i + P)];
+      for (int k = std::max(0, i - q); k < j; ++k) s -= Lij(i, k) * Lij(j, k);
+      if (i == j) {
+        if (!(s > 0.0)) return false;
+        Lij(i, i) = std::sqrt(s);
+      } else {
+        Lij(i, j) = s / Lij(j, j);
+      }
+    }
+  Lb.assign((size_t)(m + q) * q, 0.0);
+  dinv.assign(m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    for (int t = 0; t < q; ++t)
+      if (i - q + t >= 0) Lb[(size_t)i * q + t] = Lij(i, i - q + t);
+    dinv[i] = 1.0 / Lij(i, i);
+  }
+  return true;
+}
+
 Band coarsen(const Band& X) {
   // Xc = P1^T X P1 with column J of P1 holding (1/2, 1, 1/2) on rows 2J, 2J+1, 2J+2
   // (0-based; rows >= m dropped).  The coarse half-band stays <= P.

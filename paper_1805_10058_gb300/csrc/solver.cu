@@ -854,35 +854,14 @@ cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int n
 // half-bandwidth q = p - 1, in FP64 on the host; FP64 and FP32 copies on the device.
 static cd_status ensure_tband(cd_solver h) {
   if (h->have_tband) return CD_OK;
-  const int m = h->m, q = h->p - 1, P = h->P, W = 2 * P + 1;
-  if (q > 5) {
+  if (h->p - 1 > 5) {
     set_error("banded T solve: p <= 6");
     return CD_EINVAL;
   }
-  Band T;
-  toeplitz_T_band(h->p, m, P, T);
-  auto Tij = [&](int i, int j) { return T.v[(size_t)i * W + (j - i + P)]; };
-  std::vector<double> L((size_t)m * (q + 1), 0.0);  // L[i][t] = L(i, i - q + t), t = q diagonal
-  auto Lij = [&](int i, int j) -> double& { return L[(size_t)i * (q + 1) + (j - i + q)]; };
-  for (int i = 0; i < m; ++i)
-    for (int j = std::max(0, i - q); j <= i; ++j) {
-      double s = Tij(i, j);
-      for (int k = std::max(0, i - q); k < j; ++k) s -= Lij(i, k) * Lij(j, k);
-      if (i == j) {
-        if (!(s > 0.0)) {
-          set_error("banded Cholesky of T failed (not positive definite)");
-          return CD_EINVAL;
-        }
-        Lij(i, i) = std::sqrt(s);
-      } else {
-        Lij(i, j) = s / Lij(j, j);
-      }
-    }
-  std::vector<double> Lb((size_t)(m + q) * q, 0.0), dinv(m);
-  for (int i = 0; i < m; ++i) {
-    for (int t = 0; t < q; ++t)
-      if (i - q + t >= 0) Lb[(size_t)i * q + t] = Lij(i, i - q + t);
-    dinv[i] = 1.0 / Lij(i, i);
+  std::vector<double> Lb, dinv;
+  if (!tband_factor(h->p, h->m, Lb, dinv)) {
+    set_error("banded Cholesky of T failed (not positive definite)");
+    return CD_EINVAL;
   }
   if (Lb.empty()) Lb.push_back(0.0);
   if (upload(h->TB64, Lb) != cudaSuccess || upload(h->TBd64, dinv) != cudaSuccess ||
@@ -892,6 +871,71 @@ static cd_status ensure_tband(cd_solver h) {
     return CD_ECUDA;
   }
   h->have_tband = true;
+  return CD_OK;
+}
+
+// ------------------------------------------------------------------ host-only set-up queries
+static bool setup_args_ok(int p, int n) {
+  if (p < 1 || p > 6 || n < 1 || n + p - 2 < 1) {
+    set_error("need 1 <= p <= 6, n >= 1, n + p - 2 >= 1");
+    return false;
+  }
+  return true;
+}
+
+cd_status cd_setup_bands(int p, int n, int level, double* M, double* A, double* S, int* m_out,
+                         int* P_out) {
+  if (!setup_args_ok(p, n) || level < 0) return CD_EINVAL;
+  Band Mb, Ab, Sb;
+  iga_bands(p, n, p, Mb, Ab, Sb);
+  for (int l = 0; l < level; ++l) {
+    if (Mb.m / 2 < 1) {
+      set_error("cd_setup_bands: level below the coarsest grid");
+      return CD_EINVAL;
+    }
+    Mb = coarsen(Mb);
+    Ab = coarsen(Ab);
+    Sb = coarsen(Sb);
+  }
+  if (m_out) *m_out = Mb.m;
+  if (P_out) *P_out = Mb.P;
+  const size_t bytes = Mb.v.size() * sizeof(double);
+  if (M) std::memcpy(M, Mb.v.data(), bytes);
+  if (A) std::memcpy(A, Ab.v.data(), bytes);
+  if (S) std::memcpy(S, Sb.v.data(), bytes);
+  return CD_OK;
+}
+
+cd_status cd_setup_eig(int p, int n, int which, double* U, double* lam) {
+  if (!setup_args_ok(p, n) || (which != 0 && which != 1)) return CD_EINVAL;
+  const int m = n + p - 2;
+  std::vector<double> Uv, lv;
+  if (which == 0) {
+    Band Mb, Ab, Sb;
+    iga_bands(p, n, p, Mb, Ab, Sb);
+    if (!gen_eig(m, band_to_dense(Mb), band_to_dense(Sb), Uv, lv)) {
+      set_error("generalized eigen-decomposition failed");
+      return CD_EINVAL;
+    }
+  } else {
+    Band T;
+    toeplitz_T_band(p, m, p, T);
+    sym_eig(m, band_to_dense(T), Uv, lv);
+  }
+  if (U) std::memcpy(U, Uv.data(), Uv.size() * sizeof(double));
+  if (lam) std::memcpy(lam, lv.data(), lv.size() * sizeof(double));
+  return CD_OK;
+}
+
+cd_status cd_setup_tband(int p, int n, double* Lb, double* dinv) {
+  if (!setup_args_ok(p, n)) return CD_EINVAL;
+  std::vector<double> l, dv;
+  if (!tband_factor(p, n + p - 2, l, dv)) {
+    set_error("banded Cholesky of T failed (not positive definite)");
+    return CD_EINVAL;
+  }
+  if (Lb) std::memcpy(Lb, l.data(), l.size() * sizeof(double));
+  if (dinv) std::memcpy(dinv, dv.data(), dv.size() * sizeof(double));
   return CD_OK;
 }
 

@@ -88,6 +88,9 @@ def load(path=LIB_PATH):
         "cd_prolong": (i, [vp, i, vp, vp, i]),
         "cd_kernel_launches": (ctypes.c_uint64, []),
         "cd_apply3d_static": (i, [i, i, d, d, vp, vp, i, vp]),
+        "cd_setup_bands": (i, [i, i, i, dp, dp, dp, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "cd_setup_eig": (i, [i, i, i, dp, dp]),
+        "cd_setup_tband": (i, [i, i, dp, dp]),
         "cd_server_default_options": (None, [ctypes.POINTER(ServerOptions)]),
         "cd_server_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(ServerOptions)]),
         "cd_server_submit": (i, [vp, i, i, i, dp, dp, dp, i, ctypes.POINTER(ctypes.c_uint64)]),
@@ -125,6 +128,37 @@ def cd_dofs(d, p, n):
 
 def cd_kernel_launches():
     return int(load().cd_kernel_launches())
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def cd_setup_bands(p, n, level=0):
+    """Host-only: the library's 1D bands (M, A, S) of grid level `level`, each (m, 2P+1)."""
+    lib = load()
+    m, P = ctypes.c_int(), ctypes.c_int()
+    _check(lib.cd_setup_bands(p, n, level, None, None, None, ctypes.byref(m), ctypes.byref(P)),
+           "cd_setup_bands")
+    out = [np.zeros((m.value, 2 * P.value + 1)) for _ in range(3)]
+    _check(lib.cd_setup_bands(p, n, level, *[_dp(x) for x in out], None, None), "cd_setup_bands")
+    return out, P.value
+
+
+def cd_setup_eig(p, n, which):
+    """Host-only: FD eigenbasis (U, lam) of (p, n); which = 0 generalized (S, M), 1 T."""
+    m = n + p - 2
+    U, lam = np.zeros((m, m)), np.zeros(m)
+    _check(load().cd_setup_eig(p, n, which, _dp(U), _dp(lam)), "cd_setup_eig")
+    return U, lam
+
+
+def cd_setup_tband(p, n):
+    """Host-only: banded Cholesky factor of T (Lb of shape (m + q, q), dinv of length m)."""
+    m, q = n + p - 2, p - 1
+    Lb, dinv = np.zeros(max(1, (m + q) * q)), np.zeros(m)
+    _check(load().cd_setup_tband(p, n, _dp(Lb), _dp(dinv)), "cd_setup_tband")
+    return Lb[:(m + q) * q].reshape(m + q, q), dinv
 
 
 def cd_apply3d_static(p, n, alpha, beta, w, y, stream=None, check=True):
