@@ -21,7 +21,8 @@ def lib():
 def declared_symbols():
     names = set()
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
-        src = open(h).read()
+        with open(h) as f:
+            src = f.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names.update(re.findall(r"CD_API\s+[\w\s\*]+?\b(cd_\w+)\s*\(", src))
     return sorted(names)

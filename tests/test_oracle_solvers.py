@@ -34,11 +34,11 @@ def test_gauss_seidel_is_the_componentwise_sweep():
 def test_T_solver_equals_dense_kronecker_solve():
     d, p, m = 2, 3, 7
     T1 = iga1d.toeplitz_T(p, m)
-    T = sp.kron(sp.identity(d), sp.kron(T1, T1)).toarray()
+    T = np.kron(np.eye(d), np.kron(T1, T1))
     r = np.random.default_rng(2).normal(size=d * m * m)
     np.testing.assert_allclose(solvers.TSolver(d, p, m)(r), np.linalg.solve(T, r), rtol=1e-12)
     d = 3
-    T = sp.kron(sp.identity(d), sp.kron(T1, sp.kron(T1, T1))).toarray()
+    T = np.kron(np.eye(d), np.kron(T1, np.kron(T1, T1)))
     r = np.random.default_rng(3).normal(size=d * m ** 3)
     ref = np.linalg.solve(T, r)
     np.testing.assert_allclose(solvers.TSolver(d, p, m)(r), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
