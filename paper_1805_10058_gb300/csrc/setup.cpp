@@ -2,6 +2,7 @@
 // bands, and small dense eigen-decompositions.  All of it is O(m p^2) or O(m^3) with
 // m <= a few hundred and runs once per (p, n); results are cached by the solver.
 #include <algorithm>
+#include <limits>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -219,56 +220,120 @@ std::vector<double> band_to_dense(const Band& X) {
 
 // Cyclic Jacobi eigen-decomposition of a dense symmetric matrix (row-major, FP64):
 // rotations chosen to annihilate a_pq (Golub & Van Loan, symmetric Schur step).
+// Symmetric eigen-decomposition A = U diag(lam) U^T, lam ascending, U orthogonal (columns =
+// eigenvectors).  Householder reduction to tridiagonal form, then implicit symmetric QR steps
+// with the Wilkinson shift (Golub & Van Loan, Matrix Computations, Sections 8.3.1-8.3.3).  The
+// orthogonal factor is kept transposed (row j of Qt = column j of Q) so that every reflection
+// and rotation updates contiguous rows.
 bool sym_eig(int m, const std::vector<double>& Ain, std::vector<double>& U,
              std::vector<double>& lam) {
-  std::vector<double> a = Ain;
-  U.assign((size_t)m * m, 0.0);
-  for (int i = 0; i < m; ++i) U[(size_t)i * m + i] = 1.0;
-  auto at = [&](int i, int j) -> double& { return a[(size_t)i * m + j]; };
-  double fro = 0.0;
-  for (double v : a) fro += v * v;
-  fro = std::sqrt(fro);
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = i + 1; j < m; ++j) off += at(i, j) * at(i, j);
-    if (std::sqrt(off) <= 1e-17 * fro) break;
-    for (int p = 0; p < m - 1; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        const double apq = at(p, q);
-        if (std::fabs(apq) <= 1e-300) continue;
-        const double theta = (at(q, q) - at(p, p)) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < m; ++k) {  // columns p, q
-          const double akp = at(k, p), akq = at(k, q);
-          at(k, p) = c * akp - s * akq;
-          at(k, q) = s * akp + c * akq;
-        }
-        for (int k = 0; k < m; ++k) {  // rows p, q
-          const double apk = at(p, k), aqk = at(q, k);
-          at(p, k) = c * apk - s * aqk;
-          at(q, k) = s * apk + c * aqk;
-        }
-        at(p, q) = at(q, p) = 0.0;
-        for (int k = 0; k < m; ++k) {
-          double* row = &U[(size_t)k * m];
-          const double ukp = row[p], ukq = row[q];
-          row[p] = c * ukp - s * ukq;
-          row[q] = s * ukp + c * ukq;
-        }
+  std::vector<double> a = Ain, Qt((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) Qt[(size_t)i * m + i] = 1.0;
+  auto A = [&](int i, int j) -> double& { return a[(size_t)i * m + j]; };
+  // 1. tridiagonalisation: for column k, the reflection H = I - tau v v^T (v on rows k+1..)
+  //    maps A(k+1.., k) to alpha e_1; the trailing block becomes H B H = B - v w^T - w v^T with
+  //    p = tau B v, w = p - (tau/2)(p^T v) v; Q <- Q H.
+  std::vector<double> v(m), pv(m), u(m);
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n0 = k + 1, len = m - n0;
+    double nrm = 0.0;
+    for (int i = 0; i < len; ++i) nrm += A(n0 + i, k) * A(n0 + i, k);
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) continue;
+    const double x0 = A(n0, k);
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    for (int i = 0; i < len; ++i) v[i] = A(n0 + i, k);
+    v[0] = x0 - alpha;
+    double vv = 0.0;
+    for (int i = 0; i < len; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) continue;
+    const double tau = 2.0 / vv;
+    for (int i = 0; i < len; ++i) {  // p = tau B v
+      const double* row = &a[(size_t)(n0 + i) * m + n0];
+      double sum = 0.0;
+      for (int j = 0; j < len; ++j) sum += row[j] * v[j];
+      pv[i] = tau * sum;
+    }
+    double pTv = 0.0;
+    for (int i = 0; i < len; ++i) pTv += pv[i] * v[i];
+    const double K = 0.5 * tau * pTv;
+    for (int i = 0; i < len; ++i) pv[i] -= K * v[i];  // w
+    for (int i = 0; i < len; ++i) {
+      double* row = &a[(size_t)(n0 + i) * m + n0];
+      const double vi = v[i], wi = pv[i];
+      for (int j = 0; j < len; ++j) row[j] -= vi * pv[j] + wi * v[j];
+    }
+    A(n0, k) = A(k, n0) = alpha;
+    for (int i = 1; i < len; ++i) A(n0 + i, k) = A(k, n0 + i) = 0.0;
+    // Q <- Q H: rows n0.. of Qt: Qt_j -= tau v_j (sum_l v_l Qt_l)
+    std::fill(u.begin(), u.end(), 0.0);
+    for (int l = 0; l < len; ++l) {
+      const double* row = &Qt[(size_t)(n0 + l) * m];
+      const double vl = v[l];
+      for (int i = 0; i < m; ++i) u[i] += vl * row[i];
+    }
+    for (int l = 0; l < len; ++l) {
+      double* row = &Qt[(size_t)(n0 + l) * m];
+      const double f = tau * v[l];
+      for (int i = 0; i < m; ++i) row[i] -= f * u[i];
+    }
+  }
+  std::vector<double> d(m), e(std::max(m - 1, 1), 0.0);
+  for (int i = 0; i < m; ++i) d[i] = A(i, i);
+  for (int i = 0; i + 1 < m; ++i) e[i] = A(i + 1, i);
+  // 2. implicit QR steps on the unreduced block [l, h] of the tridiagonal (d, e)
+  auto rotate_rows = [&](int k, double c, double s) {  // Q <- Q R^T on columns k, k+1
+    double* rk = &Qt[(size_t)k * m];
+    double* rk1 = &Qt[(size_t)(k + 1) * m];
+    for (int i = 0; i < m; ++i) {
+      const double x = rk[i], y = rk1[i];
+      rk[i] = c * x - s * y;
+      rk1[i] = s * x + c * y;
+    }
+  };
+  const double eps = std::numeric_limits<double>::epsilon();
+  int h = m - 1, iters = 0;
+  while (h > 0) {
+    for (int i = 0; i < h; ++i)
+      if (std::fabs(e[i]) <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1]))) e[i] = 0.0;
+    if (e[h - 1] == 0.0) {
+      --h;
+      continue;
+    }
+    int l = h - 1;
+    while (l > 0 && e[l - 1] != 0.0) --l;
+    if (++iters > 60 * m) return false;
+    // Wilkinson shift from the trailing 2 x 2 block
+    const double del = 0.5 * (d[h - 1] - d[h]), bh = e[h - 1];
+    const double mu = d[h] - bh * bh / (del + (del >= 0.0 ? 1.0 : -1.0) * std::hypot(del, bh));
+    double x = d[l] - mu, z = e[l];
+    for (int k = l; k < h; ++k) {
+      // rotation R = [[c, -s], [s, c]] on rows / columns k, k+1 with R [x; z] = [r; 0]
+      const double r = std::hypot(x, z);
+      const double c = r == 0.0 ? 1.0 : x / r, s = r == 0.0 ? 0.0 : -z / r;
+      if (k > l) e[k - 1] = r;  // the bulge at (k+1, k-1) is annihilated
+      const double ak = d[k], bk = e[k], qk = d[k + 1];
+      d[k] = c * c * ak - 2.0 * c * s * bk + s * s * qk;
+      d[k + 1] = s * s * ak + 2.0 * c * s * bk + c * c * qk;
+      e[k] = c * s * (ak - qk) + (c * c - s * s) * bk;
+      if (k + 1 < h) {  // the column rotation reaches row k+2: new bulge at (k+2, k)
+        z = -s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+        x = e[k];
       }
+      rotate_rows(k, c, s);
+    }
   }
   std::vector<int> order(m);
   std::iota(order.begin(), order.end(), 0);
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return at(x, x) < at(y, y); });
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return d[x] < d[y]; });
   lam.resize(m);
-  std::vector<double> Us((size_t)m * m);
+  U.assign((size_t)m * m, 0.0);
   for (int c = 0; c < m; ++c) {
-    lam[c] = at(order[c], order[c]);
-    for (int i = 0; i < m; ++i) Us[(size_t)i * m + c] = U[(size_t)i * m + order[c]];
+    lam[c] = d[order[c]];
+    const double* q = &Qt[(size_t)order[c] * m];
+    for (int i = 0; i < m; ++i) U[(size_t)i * m + c] = q[i];
   }
-  U.swap(Us);
   return true;
 }
 
