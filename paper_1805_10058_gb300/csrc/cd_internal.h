@@ -42,7 +42,8 @@ void iga_bands(int p, int n, int P, Band& M, Band& A, Band& S);
 void toeplitz_T_band(int p, int m, int P, Band& T);
 // Galerkin coarsening of a 1D band with the 3-tap prolongator (1/2, 1, 1/2).
 Band coarsen(const Band& X);
-// Dense symmetric (generalized) eigen-decompositions, FP64, cyclic Jacobi.
+// Dense symmetric (generalized) eigen-decompositions, FP64: Householder tridiagonalisation and
+// implicit shifted QR (generalized: Cholesky reduction of M first).
 // gen = true: solve S U = M U lam with U^T M U = I (M SPD); else T U = U lam.
 bool sym_eig(int m, const std::vector<double>& Adense, std::vector<double>& U,
              std::vector<double>& lam);
