@@ -181,8 +181,8 @@ __global__ void __launch_bounds__(256) apply2d_kernel(int m, int P, int TR,
     if (mode == 1) {
       y1 = rhs[o1] - y1;
       y2 = rhs[o2] - y2;
-      acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
-    } else {
+      if (dotp) acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
+    } else if (dotp) {
       acc += (double)sw[(size_t)(r + P) * m + j] * (double)y1 +
              (double)sw[(size_t)(HR + r + P) * m + j] * (double)y2;
     }
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
       if (mode == 1) {
         y1 = rhs[o1 + jj] - y1;
         y2 = rhs[o2 + jj] - y2;
-        acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
+        if (dotp) acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
       } else if (dotp) {
         acc += (double)w1[(long long)i * m + jj] * (double)y1 + (double)w2[(long long)i * m + jj] * (double)y2;
       }
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel
         if (mode == 1) {
           y1 = rhs[o1] - y1;
           y2 = rhs[o2] - y2;
-          acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
+          if (dotp) acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
         } else if (dotp) {
           acc += (double)w[o1] * (double)y1 + (double)w[o2] * (double)y2;
         }
@@ -994,7 +994,7 @@ __global__ void __launch_bounds__(32 * T2, 2) apply3d_stream_kernel(
         } else if (mode == 1) {
           const T r = rhs[o] - v;
           y[o] = r;
-          dacc += (double)r * (double)r;
+          if (dotp) dacc += (double)r * (double)r;
         } else {
           y[o] = v;
           if (dotp) dacc += (double)w[o] * (double)v;
@@ -1118,8 +1118,8 @@ __global__ void __launch_bounds__(256) post3d_kernel(long long N, const T* __res
     if (mode == 1) {
       v = rhs[base + i] - v;
       y[base + i] = v;
-      acc += (double)v * (double)v;
-    } else {
+      if (dotp) acc += (double)v * (double)v;
+    } else if (dotp) {
       acc += (double)w[base + i] * (double)v;
     }
   }
