@@ -105,8 +105,11 @@ typedef struct {
   int fd_tensor_cores; /* FP32 FD transforms on tcgen05 (TF32 operands, FP32
                           accumulation; the Krylov method is then flexible) (1)   */
   int autotune;        /* time the tilings of the FP32 2D apply for this shape at
-                          cd_create and keep the fastest; tilings give identical
-                          results, so the choice never changes a solve (1)        */
+                          cd_create and keep the fastest (1).  Tilings give
+                          identical apply outputs; the fused dot partials are
+                          grouped by tile, so a solve's last bits can depend on
+                          the tiling, which is chosen once per (precision, m, p)
+                          and process (solves stay bit-identical within it)      */
   int reserved[6];
 } cd_options;
 
