@@ -186,6 +186,7 @@ def sine_field(ks):
     d = ks.shape[0]
 
     def field(*xs):
+        """(u, du): the d components at the points xs and their first derivatives du[c][l]."""
         u, du = [], []
         for c in range(d):
             f = [np.sin(ks[c, l] * np.pi * xs[l]) for l in range(d)]

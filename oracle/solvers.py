@@ -198,6 +198,7 @@ class Hierarchy:
 
     @property
     def levels(self):
+        """Number of levels, the finest included."""
         return len(self.A)
 
 
