@@ -102,3 +102,12 @@ def test_mass_matrix_spectrum_follows_m_p():
     ev = np.sort(np.linalg.eigvalsh(n * M))
     samp = np.sort(symbols.m_sym(p, np.arange(1, m + 1) * np.pi / m))
     assert np.max(np.abs(ev - samp)) < 0.05
+
+
+def test_3d_one_third_of_spectrum_near_zero_for_small_beta():
+    """3D, beta = 0.01: about one third of the spectrum is almost zero (Section 5.3)."""
+    p, n = 3, 8
+    A = assemble.galerkin_kron(3, p, n, 1.0, 0.01).toarray() * n
+    ev = np.linalg.eigvalsh(A)
+    frac = np.mean(ev < 0.02 * ev.max())
+    assert 0.23 < frac < 0.43, frac
