@@ -165,10 +165,11 @@ CD_API cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host
 /* One application z = B^{-1} r of a preconditioner kind (CD_PC_FD_D: D^{-1},
  * eq:diag; CD_PC_FD_T and CD_PC_T_BAND: T^{-1}, eq:kron_precond; CD_PC_MG: one
  * V-cycle from zero) in FP64 (`f32` = 0) or FP32 (`f32` = 1, pointers then hold
- * floats).
- * Device pointers.  CD_EINVAL if the handle was created without the data the
- * kind needs (FD kinds need an FD preconditioner or CD_PC_MG needs... see
- * cd_create: every handle builds all three). */
+ * floats).  r, z: device pointers, nrhs right-hand sides in the layout above;
+ * r and z may not overlap.  The data a kind needs is built on its first use
+ * (the eigenbases for the FD kinds, the banded factor for CD_PC_T_BAND; the
+ * multigrid hierarchy exists from cd_create).  CD_EINVAL for an unknown kind,
+ * CD_PC_T_BAND with p > 6, or the argument errors listed at the top. */
 CD_API cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs,
                             const double* alphas, const double* betas, int f32);
 
