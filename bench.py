@@ -185,13 +185,20 @@ def cpu_baseline_sample():
     jobs = [(PS[k % 2], 100 + k) for k in range(cores)]
     old = os.environ.get("OMP_NUM_THREADS")
     os.environ["OMP_NUM_THREADS"] = "1"  # one thread per process
+    ex = None
     try:
-        with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
-            list(ex.map(_oracle_solve_job, jobs[:1]))  # start-up outside the timing
-            t0 = time.perf_counter()
-            list(ex.map(_oracle_solve_job, jobs))
-            dtn = time.perf_counter() - t0
+        ex = cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
+        list(ex.map(_oracle_solve_job, jobs[:1], timeout=300))  # start-up outside the timing
+        t0 = time.perf_counter()
+        list(ex.map(_oracle_solve_job, jobs, timeout=300))
+        dtn = time.perf_counter() - t0
+        ex.shutdown(wait=True)
     except Exception as exc:  # the pool could not run here: report the one-core sample
+        if ex is not None:  # stop this pool's own workers without waiting on them
+            procs = list(getattr(ex, "_processes", {}).values())
+            ex.shutdown(wait=False, cancel_futures=True)
+            for pr in procs:
+                pr.kill()
         one_core["sample"] += f" (parallel sample unavailable: {type(exc).__name__})"
         return one_core
     finally:
