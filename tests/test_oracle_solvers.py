@@ -21,14 +21,25 @@ def test_direct_solve_matches_dense_cholesky(d, p, n, beta):
     assert np.linalg.norm(b - A @ x) <= 1e-13 * np.linalg.norm(b) * max(1.0, beta)
 
 
-def test_gauss_seidel_is_the_componentwise_sweep():
+def test_gauss_seidel_is_the_symmetric_componentwise_sweep():
+    """One Gauss-Seidel iteration = a forward sweep over the unknowns, then a backward one."""
     A = assemble.galerkin_kron(2, 2, 4, 1.0, 0.3).toarray()
     rng = np.random.default_rng(1)
     b, x = rng.normal(size=A.shape[0]), rng.normal(size=A.shape[0])
     ref = x.copy()
     for i in range(A.shape[0]):
         ref[i] = (b[i] - A[i, :i] @ ref[:i] - A[i, i + 1:] @ ref[i + 1:]) / A[i, i]
-    np.testing.assert_allclose(solvers.gauss_seidel(sp.csr_matrix(A), x, b), ref, rtol=1e-12)
+    fwd = ref.copy()
+    for i in reversed(range(A.shape[0])):
+        ref[i] = (b[i] - A[i, :i] @ ref[:i] - A[i, i + 1:] @ ref[i + 1:]) / A[i, i]
+    Asp = sp.csr_matrix(A)
+    np.testing.assert_allclose(solvers.gauss_seidel(Asp, x, b, symmetric=False), fwd, rtol=1e-12)
+    np.testing.assert_allclose(solvers.gauss_seidel(Asp, x, b), ref, rtol=1e-12)
+    # the symmetric sweep is the SPD splitting x' = x + (D+U)^{-1} D (D+L)^{-1} (b - A x)
+    D, L, U = np.diag(np.diag(A)), np.tril(A, -1), np.triu(A, 1)
+    Bsgs = np.linalg.solve(D + U, D @ np.linalg.solve(D + L, np.eye(A.shape[0])))
+    np.testing.assert_allclose(ref, x + Bsgs @ (b - A @ x), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(Bsgs, Bsgs.T, atol=1e-10 * np.abs(Bsgs).max())
 
 
 def test_T_solver_equals_dense_kronecker_solve():
@@ -121,23 +132,111 @@ def test_cg_counts_match_tables(row):
     assert abs(k - row["cg"]) <= 2, (k, row["cg"])
 
 
-MG_ROWS = _rows(lambda r: r["d"] == 2 and r["p"] in (1, 2, 3) and r["n"] + r["p"] - 1 <= 32)
+MG_ROWS = _rows(lambda r: (r["d"] == 2 and r["p"] in (1, 2, 3) and r["n"] + r["p"] - 1 <= 32)
+                or (r["d"] == 3 and r["n"] + r["p"] - 1 == 8 and r["p"] <= 3))
+
+
+def _within(k, ref, rel, slack=2):
+    return abs(k - ref) <= max(slack, rel * ref)
+
+
+def _strategies(row):
+    A, b, d, p, m = _case(row)
+    k_mim = solvers.mim(A, b, d, p, m)[1]
+    k_pm = solvers.p_mim(A, b, d, p, m)[1]
+    k_wl = solvers.p_wl(A, b, d, p, m)[1] if row["pwl"] is not None else None
+    return k_mim, k_pm, k_wl
+
+
+def _bands_hold(row, ks):
+    """The oracle's bands around Tables 1-4: MIM within +-2 or 15%, P_MIM within +-2, P_WL
+    within +-2 or 20% of the printed counts."""
+    k_mim, k_pm, k_wl = ks
+    ok = _within(k_mim, row["mim"], 0.15) and _within(k_pm, row["pmim"], 0.0)
+    if k_wl is not None:
+        ok = ok and _within(k_wl, row["pwl"], 0.20)
+    return ok
 
 
 @pytest.mark.parametrize("row", MG_ROWS, ids=lambda r: f"{r['table']}-p{r['p']}-n{r['n']}")
-def test_multigrid_strategies_follow_tables(row):
-    """MIM and P_WL within a loose factor of Tables 1-2; P_MIM beats MIM (Section 6.2).
+def test_multigrid_strategies_match_tables(row):
+    """MIM, P_MIM and P_WL (Section 6.2) against Tables 1-4.  Readings: symmetric Gauss-Seidel
+    sweeps, two V-cycles per P_MIM preconditioner application (the design notes list both)."""
+    ks = _strategies(row)
+    assert _bands_hold(row, ks), (ks, row["mim"], row["pmim"], row["pwl"])
 
-    The paper does not fix its smoothing order, orthogonalisation or outer-CG variant, so
-    these counts are not expected to match exactly (the differences are listed in the
-    design notes)."""
+
+# Plausible mistakes planted in the oracle (on the CPU): each must break the bands above on at
+# least one of two Table 1-2 rows, so the bands really pin the V-cycle.
+def _no_coarse_correction(H, b, x, fine_post, level=0):
+    A = H.A[level]
+    if level == H.levels - 1:
+        return H.coarse_lu.solve(b)
+    x = solvers.gauss_seidel(A, x, b)
+    return fine_post(A, b, x) if level == 0 else solvers.gauss_seidel(A, x, b)
+
+
+def _half_restriction(H, b, x, fine_post, level=0):
+    A = H.A[level]
+    if level == H.levels - 1:
+        return H.coarse_lu.solve(b)
+    x = solvers.gauss_seidel(A, x, b)
+    rc = 0.5 * (H.P[level].T @ (b - A @ x))
+    x = x + H.P[level] @ _half_restriction(H, rc, np.zeros(rc.size), fine_post, level + 1)
+    return fine_post(A, b, x) if level == 0 else solvers.gauss_seidel(A, x, b)
+
+
+class _IdentityT:
+    def __init__(self, d, p, m):
+        pass
+
+    def __call__(self, r):
+        return r
+
+
+def _shifted_prolongator(d, m):
+    mc = m // 2
+    rows, cols, vals = [], [], []
+    for j in range(mc):
+        for off, v in ((-1, 0.5), (0, 1.0), (1, 0.5)):
+            if 0 <= 2 * j + off < m:
+                rows.append(2 * j + off)
+                cols.append(j)
+                vals.append(v)
+    P1 = sp.csr_matrix((vals, (rows, cols)), shape=(m, mc))
+    out = sp.identity(d, format="csr")
+    for _ in range(d):
+        out = sp.kron(out, P1, format="csr")
+    return out.tocsr()
+
+
+_forward_gs = solvers.gauss_seidel
+
+
+MISTAKES = {
+    "no coarse-grid correction": ("vcycle", _no_coarse_correction),
+    "restriction scaled by 1/2": ("vcycle", _half_restriction),
+    "forward Gauss-Seidel only": ("gauss_seidel", lambda A, x, b: _forward_gs(A, x, b, False)),
+    "T replaced by the identity": ("TSolver", _IdentityT),
+    "prolongator columns off by one row": ("block_prolongator", _shifted_prolongator),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MISTAKES))
+def test_planted_multigrid_mistakes_break_the_bands(name, monkeypatch):
+    attr, repl = MISTAKES[name]
+    monkeypatch.setattr(solvers, attr, repl)
+    rows = [r for r in paper_tables() if r["d"] == 2 and r["p"] == 2 and r["n"] == 15]
+    assert len(rows) == 2
+    assert not all(_bands_hold(r, _strategies(r)) for r in rows), name
+
+
+def test_one_vcycle_p_mim_misses_the_table():
+    """The other reading of P_MIM (one V-cycle per application) gives ~1.5x the printed counts."""
+    row = [r for r in paper_tables() if r["table"] == "T2" and r["p"] == 2 and r["n"] == 15][0]
     A, b, d, p, m = _case(row)
-    _, k_mim = solvers.mim(A, b, d, p, m)
-    _, k_wl = solvers.p_wl(A, b, d, p, m)
-    _, k_pm = solvers.p_mim(A, b, d, p, m)
-    assert 0.6 * row["mim"] <= k_mim <= 2.0 * row["mim"] + 2, (k_mim, row["mim"])
-    assert 0.6 * row["pwl"] <= k_wl <= 2.0 * row["pwl"] + 2, (k_wl, row["pwl"])
-    assert k_pm < k_mim and k_pm < 0.2 * row["cg"] + 30
+    k1 = solvers.p_mim(A, b, d, p, m, cycles=1)[1]
+    assert k1 > row["pmim"] + 5, k1
 
 
 def test_p_mim_is_flat_in_n():
@@ -146,7 +245,7 @@ def test_p_mim_is_flat_in_n():
         row = dict(d=2, p=2, n=n, beta=0.1)
         A, b, d, p, m = _case(row)
         ks.append(solvers.p_mim(A, b, d, p, m)[1])
-    assert max(ks) - min(ks) <= 3, ks
+    assert max(ks) - min(ks) <= 1, ks
 
 
 def _fp64_floor(p, n, beta):
