@@ -110,15 +110,24 @@ typedef struct {
                           grouped by tile, so a solve's last bits can depend on
                           the tiling, which is chosen once per (precision, m, p)
                           and process (solves stay bit-identical within it)      */
-  int reserved[6];
+  int ext_residual;    /* 1 (default): the outer loop keeps the solution as an unevaluated
+                          sum x_hi + x_lo of two FP64 vectors and evaluates b - A x in
+                          double-FP64 arithmetic (about 106 significant bits), so the stopping
+                          rule is not limited by FP64 rounding of A x (at beta/alpha = 1e+-6
+                          and n = 256 an FP64 evaluation bottoms out near 1e-8).  0: FP64
+                          solution and residual.                                           */
+  int reserved[5];
 } cd_options;
 
 typedef struct {
   int iters_outer;    /* refinement steps (1 for CD_PREC_FP64)                  */
   int iters_inner;    /* Krylov iterations summed over refinement steps         */
-  double relres;      /* final ||b - A x|| / ||b|| measured in FP64             */
+  double relres;      /* final ||b - A x|| / ||b|| of the solution the call returns
+                         (cd_solve: x; cd_solve_ext: x + x_lo), evaluated in double-FP64
+                         when ext_residual is set, else in FP64                    */
   double seconds;     /* wall time of the call (whole batch)                    */
-  int status;         /* cd_status of this right-hand side                      */
+  int status;         /* cd_status of this right-hand side: CD_OK iff relres <= rtol */
+  double relres_hi;   /* the same for x alone (equal to relres for cd_solve)    */
 } cd_result;
 
 /* Fills *opt with the defaults listed above. */
@@ -155,6 +164,16 @@ CD_API cd_status cd_apply_f32(cd_solver h, const float* w, float* y, int nrhs,
  * Returns the worst per-RHS status. */
 CD_API cd_status cd_solve(cd_solver h, const double* b, double* x, int nrhs,
                           const double* alphas, const double* betas, cd_result* res);
+
+/* As cd_solve, returning the solution as the unevaluated sum x + x_lo of two FP64 vectors
+ * (x = the FP64 rounding of the sum; x_lo: device FP64, same layout, may be NULL).  With
+ * ext_residual set, the refinement loop of Section 6.2's stopping rule measures
+ * ||b - A (x + x_lo)|| in double-FP64, so the rule can be met where an FP64 vector cannot
+ * represent a solution that accurate (at beta/alpha = 1e+-6 the exact solution rounded to FP64
+ * has a relative residual near 1e-10 at n = 256).  res[i].relres is that of x + x_lo and
+ * res[i].relres_hi that of x alone.  Without ext_residual x_lo is filled with zeros. */
+CD_API cd_status cd_solve_ext(cd_solver h, const double* b, double* x, double* x_lo, int nrhs,
+                              const double* alphas, const double* betas, cd_result* res);
 
 /* As cd_solve with host b and x (pageable or pinned): copies b to the device,
  * solves, copies x back; all three steps are inside the call. */
@@ -281,13 +300,16 @@ CD_API cd_status cd_server_destroy(cd_server s);
  *
  * Its working memory is a fixed 48 MiB array in the library's device image: every GPU
  * that loads the library holds it until the process exits.  A call needs about
- * 21 m^3 nrhs + 3 m (2p+1) + 2 nrhs doubles of it (m = n + p - 2; for one right-hand
- * side m <= 66); larger requests return CD_EINVAL with the limit in cd_last_error().
+ * 18 m^3 nrhs + 3 m (2p+1) + 2 nrhs doubles of it (m = n + p - 2; for one right-hand
+ * side m <= 70); larger requests return CD_EINVAL with the limit in cd_last_error().
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every call
- * shares the array and overwrites what it reads, so calls whose work overlaps on the GPU
- * (on different streams or from different threads) race.  The call uploads the 1D bands
- * with a small host-to-device copy and waits for that copy before launching. */
+ * with that device current; make that first call before any stream capture.  The address
+ * is kept per device and looked up again if the device's context was rebuilt (a
+ * cudaDeviceReset).  Every call shares the array and overwrites what it reads, so calls
+ * whose work overlaps on the GPU (on different streams or from different threads) race.
+ * The call copies the 1D bands and parameters from host memory to the array with
+ * cudaMemcpyAsync on `cuda_stream` (NULL = legacy default stream), then launches the
+ * three banded FP64 passes on it; it does not wait for the GPU. */
 CD_API cd_status cd_apply3d_static(int p, int n, double alpha, double beta, const double* w,
                                    double* y, int nrhs, void* cuda_stream);
 

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcurldiv.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["setup.cpp", "kernels.cu", "krylov.cu", "mg.cu", "solver.cu", "server.cpp",
-           "static_apply.cu", "fd_tc.cu"]
+           "static_apply.cu", "fd_tc.cu", "ext_residual.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,8 +29,6 @@ def _compile(src, extra):
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
     cmd = [nvcc(), "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-lineinfo",
            "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", CSRC] + ARCH + extra
-    if src.endswith(".cpp"):
-        cmd += ["-x", "cu"] if False else []
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -111,6 +111,18 @@ bool apply_can_fuse(int d, int m, int P, const T* bands, int B);
 // Sets kernel attributes (dynamic shared memory caps); call once before launches/captures.
 int prepare_kernels();
 
+// Extended-precision outer residual (ext_residual.cu): r = b - A (xh + xl) in double-FP64 from
+// the FP64 bands of the finest level, rounded to FP64 (xl may be NULL).  `scratch` holds
+// chunk * ext_scratch_doubles_per_solve(d, m) doubles; solves are processed `chunk` at a time.
+long long ext_scratch_doubles_per_solve(int d, int m);
+int launch_ext_residual(int d, int m, int P, const double* bands, const double* rhs,
+                        const double* xh, const double* xl, double* r, int B, Coef c,
+                        const int* active, double* scratch, int chunk, cudaStream_t s);
+// (xh, xl) += rnorm_b * e, exactly rounded into the double-FP64 pair
+template <typename E>
+void launch_ext_update(long long N, int B, double* xh, double* xl, const E* e,
+                       const double* rnorm, const int* active, cudaStream_t s);
+
 // capacity (per solve) of the block-partial-sum arrays every reduction writes into
 constexpr int kMaxPartials = 4096;
 

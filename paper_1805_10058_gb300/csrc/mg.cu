@@ -417,8 +417,6 @@ cd_status mg_build(MgData& mg, int d, int P, const std::vector<int>& ml,
   return CD_OK;
 }
 
-void mg_set_scratch(MgData&, void*, void*) {}
-
 template <typename T>
 static const T* level_bands(const MgData& mg, int l) {
   if (sizeof(T) == 8) return reinterpret_cast<const T*>(mg.bands64 + mg.boff[l]);
@@ -426,8 +424,7 @@ static const T* level_bands(const MgData& mg, int l) {
 }
 
 template <typename T>
-static T* level_scratch(MgData& mg, int l, T* fine_scratch) {
-  (void)fine_scratch;
+static T* level_scratch(MgData& mg) {
   return (T*)(sizeof(T) == 8 ? mg.scratch64 : mg.scratch32);
 }
 
@@ -553,7 +550,7 @@ static void smooth_post_fused(MgData& mg, int l, int B, const T* bl, const T* XB
 template <typename T>
 static void vcycle_rec(MgData& mg, int l, int B, const T* bl, T* xl, Coef c, const int* active,
                        T* fine_scr, cudaStream_t s) {
-  T* scr = l == 0 ? fine_scr : level_scratch<T>(mg, l, fine_scr);
+  T* scr = l == 0 ? fine_scr : level_scratch<T>(mg);
   if (l == mg.L - 1) {
     coarse_solve_kernel<T><<<B, 128, 0, s>>>(mg.nc, sizeof(T) == 8 ? (const T*)mg.cinv64 : (const T*)mg.cinv32,
                                              bl, xl, active);

@@ -89,6 +89,8 @@ struct cd_solver_s {
   DevBuf ir_rnorm, ir_bnorm2, ir_relres, ir_active, ir_status, ir_outer, ir_inner_total, cnt;
   DevBuf ir_rrprev, ir_grp, ir_tol2, ir_m0, ir_m1, ir_m2;
   DevBuf b64, x64, r64;
+  DevBuf xlo64, ext_scratch;  // low parts of the double-FP64 solution; residual intermediates
+  int ext_chunk = 0;          // solves per launch of the extended residual
   Workspace w64, w32;
   int* h_cnt = nullptr;  // pinned
   MgData mg;
@@ -317,13 +319,35 @@ __global__ void f2d_kernel(long long n, const float* a, double* b) {
     b[i] = (double)a[i];
 }
 
-// Final FP64 residual ||b - A x|| / ||b|| for reporting (FP64 apply, mode 1).
+// Outer residual r64 = b - A (x + xlo) with per-solve partial sums of r^T r in part[0]
+// (*npart partials per solve): double-FP64 when the handle keeps an extended solution (xlo
+// may then be NULL for the FP64 x alone), else the FP64 apply in residual mode.
+static cd_status outer_residual(cd_solver h, int B, const double* b, const double* x,
+                                const double* xlo, const int* active, int* npart) {
+  if (h->opt.ext_residual) {
+    if (launch_ext_residual(h->d, h->m, h->P, bands_of<double>(h, 0), b, x, xlo,
+                            h->r64.as<double>(), B, coef_of(h), active,
+                            h->ext_scratch.as<double>(), h->ext_chunk, h->s) != 0) {
+      set_error("extended residual: unsupported shape");
+      return CD_EINVAL;
+    }
+    *npart = partial_blocks(h->N);
+    launch_dot<double>(h->r64.as<double>(), h->r64.as<double>(), h->N, B, h->part[0].as<double>(),
+                       *npart, active, h->s);
+    return CD_OK;
+  }
+  apply_level<double>(h, 0, x, h->r64.as<double>(), b, 1, B, h->part[0].as<double>(), npart,
+                      active);
+  return CD_OK;
+}
+
+// Final ||b - A x|| / ||b|| per solve for reporting (same evaluation as the outer loop).
 static cd_status final_residual(cd_solver h, int B, const double* b, const double* x,
-                                std::vector<double>& relres) {
+                                const double* xlo, std::vector<double>& relres) {
   const int nb = partial_blocks(h->N);
   int npart = 0;
-  apply_level<double>(h, 0, x, h->r64.as<double>(), b, 1, B, h->part[0].as<double>(), &npart,
-                      nullptr);
+  cd_status st = outer_residual(h, B, b, x, xlo, nullptr, &npart);
+  if (st != CD_OK) return st;
   launch_dot<double>(b, b, h->N, B, h->part[1].as<double>(), nb, nullptr, h->s);
   std::vector<double> prr((size_t)B * npart), pbb((size_t)B * nb);
   CD_CUDA_OK(cudaMemcpyAsync(prr.data(), h->part[0].p, prr.size() * 8, cudaMemcpyDeviceToHost, h->s));
@@ -380,8 +404,12 @@ static cd_status set_params(cd_solver h, int nrhs, const double* alphas, const d
   return CD_OK;
 }
 
-static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd_result* res,
-                              const std::vector<double>& alphas, const std::vector<double>& betas) {
+// Solves A x = b for B right-hand sides.  With ext_residual the solution is carried as
+// x + xlo (double-FP64); `xlo_out` (may be NULL) receives the low part and decides which
+// solution the status and relres describe: x + xlo when given, x alone otherwise.
+static cd_status solve_device(cd_solver h, const double* b, double* x, double* xlo_out, int B,
+                              cd_result* res, const std::vector<double>& alphas,
+                              const std::vector<double>& betas) {
   auto t0 = std::chrono::steady_clock::now();
   const long long N = h->N;
   const int pc = h->opt.precond;
@@ -405,14 +433,17 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd
   set_int_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->ir_inner_total.as<int>(), 0);
   count_launch(4);
   vzero<double>(N, B, x, nullptr, h->s);
+  const bool ext = h->opt.ext_residual != 0;
+  double* xlo = ext ? h->xlo64.as<double>() : nullptr;
+  if (ext) vzero<double>(N, B, xlo, nullptr, h->s);
   launch_dot<double>(b, b, N, B, h->part[1].as<double>(), nb, nullptr, h->s);
   launch_sum_partials(h->part[1].as<double>(), nb, B, h->ir_bnorm2.as<double>(), h->s);
   const double inner2 = h->opt.inner_rtol * h->opt.inner_rtol;
   const double* tol2v = h->ir_tol2.as<double>();
   for (int step = 0; step <= h->opt.max_outer + 1; ++step) {
     int npart = 0;
-    apply_level<double>(h, 0, x, h->r64.as<double>(), b, 1, B, h->part[0].as<double>(), &npart,
-                        act);
+    cd_status rst = outer_residual(h, B, b, x, xlo, act, &npart);
+    if (rst != CD_OK) return rst;
     ir_check(B, h->part[0].as<double>(), npart, h->ir_bnorm2.as<double>(), h->ir_rnorm.as<double>(),
              h->ir_rrprev.as<double>(), act, h->ir_status.as<int>(), h->ir_relres.as<double>(),
              h->ir_outer.as<int>(), h->ir_grp.as<int>(), h->ir_tol2.as<double>(),
@@ -430,20 +461,31 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd
       add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), m[0],
                                                           h->ir_inner_total.as<int>());
       count_launch();
-      ir_update(N, B, x, h->w32.x.as<float>(), h->ir_rnorm.as<double>(), m[0], h->s);
+      if (ext)
+        launch_ext_update<float>(N, B, x, xlo, h->w32.x.as<float>(), h->ir_rnorm.as<double>(), m[0],
+                                 h->s);
+      else
+        ir_update(N, B, x, h->w32.x.as<float>(), h->ir_rnorm.as<double>(), m[0], h->s);
     }
     for (int g = 1; g <= 2; ++g) {
       if (cnt[g] == 0) continue;
       scale_div(N, B, h->r64.as<double>(), h->w64.r.as<double>(), h->ir_rnorm.as<double>(), m[g], h->s);
-      // the first FP64 inner solve may use the whole budget; a restart only has to correct
-      // the drift of the recursive residual (or show that the FP64 floor is reached)
-      const int cap = step == 0 ? h->opt.maxit : std::min({h->opt.maxit, h->opt.inner_maxit, 500});
+      // the first FP64 inner solve may use the whole budget.  With an FP64 outer residual a
+      // restart only has to correct the drift of the recursive residual (or show that the FP64
+      // floor is reached); with the double-FP64 residual it continues below that floor and
+      // keeps the whole budget (the outer check stops a solve at maxit iterations in total).
+      const int cap = (step == 0 || ext) ? h->opt.maxit
+                                         : std::min({h->opt.maxit, h->opt.inner_maxit, 500});
       cd_status st = run_pcg<double>(h, B, pc, tol2v, cap, m[g]);
       if (st != CD_OK) return st;
       add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), m[g],
                                                           h->ir_inner_total.as<int>());
       count_launch();
-      ir_update64(N, B, x, h->w64.x.as<double>(), h->ir_rnorm.as<double>(), m[g], h->s);
+      if (ext)
+        launch_ext_update<double>(N, B, x, xlo, h->w64.x.as<double>(), h->ir_rnorm.as<double>(),
+                                  m[g], h->s);
+      else
+        ir_update64(N, B, x, h->w64.x.as<double>(), h->ir_rnorm.as<double>(), m[g], h->s);
     }
   }
   CD_CUDA_OK(cudaMemcpyAsync(status.data(), h->ir_status.p, B * 4, cudaMemcpyDeviceToHost, h->s));
@@ -454,23 +496,40 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, int B, cd
     set_error("a tensor-core FD kernel gave up waiting for its MMAs");
     return CD_ECUDA;
   }
-  std::vector<double> rel;
-  cd_status st = final_residual(h, B, b, x, rel);
+  // x = the FP64 rounding of x + xlo already (the update renormalises the pair)
+  std::vector<double> rel_hi, rel_ext;
+  cd_status st = final_residual(h, B, b, x, nullptr, rel_hi);
   if (st != CD_OK) return st;
+  if (ext && xlo_out) {
+    st = final_residual(h, B, b, x, xlo, rel_ext);
+    if (st != CD_OK) return st;
+  } else {
+    rel_ext = rel_hi;
+  }
+  if (xlo_out) {
+    if (ext)
+      CD_CUDA_OK(cudaMemcpyAsync(xlo_out, xlo, 8 * (size_t)B * N, cudaMemcpyDeviceToDevice, h->s));
+    else
+      vzero<double>(N, B, xlo_out, nullptr, h->s);
+  }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   cd_status worst = CD_OK;
   for (int i = 0; i < B; ++i) {
     int s_i = status[i];
-    if (s_i == CD_OK && !(rel[i] <= h->opt.rtol * 10)) s_i = CD_NOT_CONVERGED;
+    // the status describes the solution returned: x + xlo when the caller takes xlo
+    const double rel = xlo_out ? rel_ext[i] : rel_hi[i];
+    if (s_i == CD_OK && !(rel <= h->opt.rtol)) s_i = CD_NOT_CONVERGED;
     if (s_i != CD_OK && worst == CD_OK) worst = (cd_status)s_i;
     if (res) {
       res[i].iters_outer = outer[i];
       res[i].iters_inner = inner[i];
-      res[i].relres = rel[i];
+      res[i].relres = rel;
+      res[i].relres_hi = rel_hi[i];
       res[i].seconds = secs;
       res[i].status = s_i;
     }
   }
+  if (xlo_out) CD_CUDA_OK(cudaStreamSynchronize(h->s));
   return worst;
 }
 
@@ -540,6 +599,10 @@ size_t solver_bytes(int d, int p, int n, const cd_options& opt) {
   if (d == 3) bytes += 21 * n3_1 * B * 12;
   if (opt.precond == CD_PC_FD_D || opt.precond == CD_PC_FD_T)
     bytes += (size_t)m * m * 12 * 4;
+  if (opt.ext_residual) {
+    const size_t per = (size_t)6 * N;  // residual intermediates (hi, lo) per solve, doubles
+    bytes += 8 * B * N + 8 * std::min(B * per, std::max(per, (size_t)(256u << 20) / 8));
+  }
   return (size_t)(1.1 * (double)bytes) + (64u << 20);
 }
 }  // namespace cd
@@ -565,6 +628,7 @@ void cd_default_options(cd_options* o) {
   o->mixed_switch_ratio = 1e4;
   o->fd_tensor_cores = 1;
   o->autotune = 1;
+  o->ext_residual = 1;
 }
 
 size_t cd_dofs(int d, int p, int n) {
@@ -741,6 +805,16 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     cudaGetLastError();
     return CD_ENOMEM;
   }
+  if (h->opt.ext_residual) {  // double-FP64 solution and residual intermediates
+    const long long per = ext_scratch_doubles_per_solve(d, m);
+    const long long budget = (256LL << 20) / 8;  // doubles of intermediates per launch group
+    h->ext_chunk = (int)std::max<long long>(1, std::min<long long>(B, budget / per));
+    if (!al(h->xlo64, 8 * (size_t)B * N) || !al(h->ext_scratch, 8 * (size_t)h->ext_chunk * per)) {
+      set_error("workspace allocation failed");
+      cudaGetLastError();
+      return CD_ENOMEM;
+    }
+  }
   if (cudaMallocHost(&h->h_cnt, 64) != cudaSuccess) return CD_ENOMEM;
   {
     cd_status st = mg_build(h->mg, d, P, h->ml, h->hM, h->hA, h->hS, B,
@@ -826,7 +900,17 @@ cd_status cd_solve(cd_solver h, const double* b, double* x, int nrhs, const doub
   std::lock_guard<std::mutex> lk(h->mu);
   std::vector<double> va, vb;
   if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond == CD_PC_MG)) != CD_OK) return st;
-  return solve_device(h, b, x, nrhs, res, va, vb);
+  return solve_device(h, b, x, nullptr, nrhs, res, va, vb);
+}
+
+cd_status cd_solve_ext(cd_solver h, const double* b, double* x, double* x_lo, int nrhs,
+                       const double* alphas, const double* betas, cd_result* res) {
+  cd_status st = check_call(h, b, x, nrhs);
+  if (st != CD_OK) return st;
+  std::lock_guard<std::mutex> lk(h->mu);
+  std::vector<double> va, vb;
+  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond == CD_PC_MG)) != CD_OK) return st;
+  return solve_device(h, b, x, x_lo, nrhs, res, va, vb);
 }
 
 cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int nrhs,
@@ -843,7 +927,7 @@ cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int n
       return CD_ENOMEM;
   }
   CD_CUDA_OK(cudaMemcpyAsync(h->b64.p, b_host, bytes, cudaMemcpyHostToDevice, h->s));
-  st = solve_device(h, h->b64.as<double>(), h->x64.as<double>(), nrhs, res, va, vb);
+  st = solve_device(h, h->b64.as<double>(), h->x64.as<double>(), nullptr, nrhs, res, va, vb);
   if (st != CD_OK && st != CD_NOT_CONVERGED && st != CD_BREAKDOWN) return st;
   CD_CUDA_OK(cudaMemcpyAsync(x_host, h->x64.p, bytes, cudaMemcpyDeviceToHost, h->s));
   CD_CUDA_OK(cudaStreamSynchronize(h->s));

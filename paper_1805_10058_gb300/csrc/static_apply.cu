@@ -18,7 +18,19 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 static std::mutex g_static_mu;
 static void* g_static_dev_ptr[128] = {};  // device address of g_static_scratch, per device
 
-// Device address of the array on the current device; looked up once per device.
+// True while `p` is still device memory of device `dev` (a cached address goes stale when the
+// process resets the device and its context is rebuilt).
+static bool still_device_ptr(void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+// Device address of the array on the current device; looked up once per device (and again if
+// the device's context was rebuilt since).
 static cd_status static_scratch_ptr(void** out) {
   int dev = 0;
   CD_CUDA_OK(cudaGetDevice(&dev));
@@ -27,6 +39,8 @@ static cd_status static_scratch_ptr(void** out) {
     return CD_EINVAL;
   }
   std::lock_guard<std::mutex> lk(g_static_mu);
+  if (g_static_dev_ptr[dev] && !still_device_ptr(g_static_dev_ptr[dev], dev))
+    g_static_dev_ptr[dev] = nullptr;
   if (!g_static_dev_ptr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
@@ -54,14 +68,15 @@ extern "C" cd_status cd_apply3d_static(int p, int n, double alpha, double beta, 
     return CD_EINVAL;
   }
   const int m = n + p - 2, P = p, W = 2 * P + 1;
-  // layout (doubles): bands [3][m][W] | alpha[nrhs] | beta[nrhs] | 21 arrays of m^3 nrhs
+  // layout (doubles): bands [3][m][W] | alpha[nrhs] | beta[nrhs] | 18 arrays of m^3 nrhs (the
+  // two groups of nine intermediates of the three banded FP64 passes, which write y directly)
   const size_t n3 = (size_t)m * m * m;
   const size_t nb = ((size_t)3 * m * W + 31) / 32 * 32;
   const size_t np = ((size_t)2 * nrhs + 31) / 32 * 32;
-  const size_t need = nb + np + (size_t)21 * n3 * nrhs;
+  const size_t need = nb + np + (size_t)18 * n3 * nrhs;
   if (need * sizeof(double) > kStaticScratchBytes) {
     set_error("cd_apply3d_static: (m, nrhs) too large for the 48 MiB static scratch (it needs about "
-              "21 m^3 nrhs + 3 m (2p+1) + 2 nrhs doubles; m = " + std::to_string(m) +
+              "18 m^3 nrhs + 3 m (2p+1) + 2 nrhs doubles; m = " + std::to_string(m) +
               ", nrhs = " + std::to_string(nrhs) + ")");
     return CD_EINVAL;
   }
@@ -83,12 +98,16 @@ extern "C" cd_status cd_apply3d_static(int p, int n, double alpha, double beta, 
     host[nb + i] = alpha;
     host[nb + nrhs + i] = beta;
   }
-  // every region the kernels read is rewritten here or by an earlier pass of this call
+  // every region the kernels read is rewritten here or by an earlier pass of this call.  The
+  // source is pageable host memory: CUDA stages it before cudaMemcpyAsync returns, so the
+  // vector may go out of scope without waiting for the copy.
   CD_CUDA_OK(cudaMemcpyAsync(dbands, host.data(), host.size() * sizeof(double),
                              cudaMemcpyHostToDevice, s));
-  CD_CUDA_OK(cudaStreamSynchronize(s));  // the host staging vector goes out of scope
-  launch_apply<double>(3, m, P, dbands, w, y, nullptr, 0, nrhs, Coef{dal, dbe}, nullptr, nullptr,
-                       nullptr, dscr, s);
+  if (launch_apply<double>(3, m, P, dbands, w, y, nullptr, 0, nrhs, Coef{dal, dbe}, nullptr,
+                           nullptr, nullptr, dscr, s) != 0) {
+    set_error("cd_apply3d_static: no apply kernel fits this problem size");
+    return CD_EINVAL;
+  }
   CD_CUDA_OK(cudaGetLastError());
   return CD_OK;
 }

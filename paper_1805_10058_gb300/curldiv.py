@@ -24,16 +24,19 @@ class Options(ctypes.Structure):
                 ("max_outer", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("mg_m_min", ctypes.c_int), ("use_graphs", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("mixed_switch_ratio", ctypes.c_double), ("fd_tensor_cores", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("autotune", ctypes.c_int), ("ext_residual", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("iters_outer", ctypes.c_int), ("iters_inner", ctypes.c_int),
-                ("relres", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+                ("relres", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int),
+                ("relres_hi", ctypes.c_double)]
 
     def as_dict(self):
         return dict(iters_outer=self.iters_outer, iters_inner=self.iters_inner,
-                    relres=self.relres, seconds=self.seconds, status=self.status)
+                    relres=self.relres, seconds=self.seconds, status=self.status,
+                    relres_hi=self.relres_hi)
 
 
 class ServerOptions(ctypes.Structure):
@@ -80,6 +83,7 @@ def load(path=LIB_PATH):
         "cd_apply_f32": (i, [vp, vp, vp, i, dp, dp]),
         "cd_solve": (i, [vp, vp, vp, i, dp, dp, ctypes.POINTER(Result)]),
         "cd_solve_host": (i, [vp, vp, vp, i, dp, dp, ctypes.POINTER(Result)]),
+        "cd_solve_ext": (i, [vp, vp, vp, vp, i, dp, dp, ctypes.POINTER(Result)]),
         "cd_precond": (i, [vp, i, vp, vp, i, dp, dp, i]),
         "cd_get_bands": (i, [vp, i, dp, dp, dp, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "cd_levels": (i, [vp]),
@@ -166,7 +170,9 @@ def cd_apply3d_static(p, n, alpha, beta, w, y, stream=None, check=True):
     import torch
     lib = load()
     N = cd_dofs(3, p, n)
-    nrhs = w.numel() // N
+    if N == 0:
+        raise ValueError("cd_apply3d_static: invalid (p, n)")
+    nrhs = _nrhs(N, w, y, "cd_apply3d_static")
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     st = lib.cd_apply3d_static(p, n, alpha, beta, _dev(w, "float64"), _dev(y, "float64"), nrhs,
@@ -174,6 +180,16 @@ def cd_apply3d_static(p, n, alpha, beta, w, y, stream=None, check=True):
     if check:
         _check(st, "cd_apply3d_static")
     return st
+
+
+def _nrhs(N, a, b, what):
+    """Right-hand sides in a pair of vectors: both must hold the same whole number (>= 1) of
+    N-entry right-hand sides (a short output would let the kernels write past its end)."""
+    na, nb = int(a.numel() if hasattr(a, "numel") else a.size), int(b.numel() if hasattr(b, "numel") else b.size)
+    if na < N or na % N or nb != na:
+        raise ValueError(f"{what}: expected two vectors of the same length nrhs * {N} (nrhs >= 1), "
+                         f"got {na} and {nb} entries")
+    return na // N
 
 
 def _params(nrhs, alphas, betas):
@@ -226,18 +242,18 @@ class Solver:
             pass
 
     def cd_apply(self, w, y, alphas=None, betas=None):
-        nrhs = w.numel() // self.N
+        nrhs = _nrhs(self.N, w, y, "cd_apply")
         keep, pa, pb = _params(nrhs, alphas, betas)
         _check(self.lib.cd_apply(self.h, _dev(w, "float64"), _dev(y, "float64"), nrhs, pa, pb), "cd_apply")
 
     def cd_apply_f32(self, w, y, alphas=None, betas=None):
-        nrhs = w.numel() // self.N
+        nrhs = _nrhs(self.N, w, y, "cd_apply_f32")
         keep, pa, pb = _params(nrhs, alphas, betas)
         _check(self.lib.cd_apply_f32(self.h, _dev(w, "float32"), _dev(y, "float32"), nrhs, pa, pb),
                "cd_apply_f32")
 
     def cd_solve(self, b, x, alphas=None, betas=None, check=True):
-        nrhs = b.numel() // self.N
+        nrhs = _nrhs(self.N, b, x, "cd_solve")
         keep, pa, pb = _params(nrhs, alphas, betas)
         res = (Result * nrhs)()
         st = self.lib.cd_solve(self.h, _dev(b, "float64"), _dev(x, "float64"), nrhs, pa, pb, res)
@@ -245,9 +261,24 @@ class Solver:
             _check(st, "cd_solve")
         return st, [r.as_dict() for r in res]
 
+    def cd_solve_ext(self, b, x, x_lo=None, alphas=None, betas=None, check=True):
+        """Solve returning the double-FP64 solution x + x_lo (x_lo may be None)."""
+        nrhs = _nrhs(self.N, b, x, "cd_solve_ext")
+        if x_lo is not None:
+            _nrhs(self.N, x, x_lo, "cd_solve_ext")
+        keep, pa, pb = _params(nrhs, alphas, betas)
+        res = (Result * nrhs)()
+        lo = _dev(x_lo, "float64") if x_lo is not None else None
+        st = self.lib.cd_solve_ext(self.h, _dev(b, "float64"), _dev(x, "float64"), lo, nrhs, pa, pb, res)
+        if check and st not in (CD_OK,):
+            _check(st, "cd_solve_ext")
+        return st, [r.as_dict() for r in res]
+
     def cd_solve_host(self, b, x, alphas=None, betas=None):
-        assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
-        nrhs = b.size // self.N
+        if not (b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous
+                and x.flags.c_contiguous):
+            raise TypeError("cd_solve_host: expected contiguous float64 numpy arrays")
+        nrhs = _nrhs(self.N, b, x, "cd_solve_host")
         keep, pa, pb = _params(nrhs, alphas, betas)
         res = (Result * nrhs)()
         st = self.lib.cd_solve_host(self.h, ctypes.c_void_p(b.ctypes.data), ctypes.c_void_p(x.ctypes.data),
@@ -256,7 +287,7 @@ class Solver:
 
     def cd_precond(self, kind, r, z, alphas=None, betas=None):
         f32 = str(r.dtype) == "torch.float32"
-        nrhs = r.numel() // self.N
+        nrhs = _nrhs(self.N, r, z, "cd_precond")
         keep, pa, pb = _params(nrhs, alphas, betas)
         dt = "float32" if f32 else "float64"
         _check(self.lib.cd_precond(self.h, kind, _dev(r, dt), _dev(z, dt), nrhs, pa, pb, int(f32)),
@@ -283,13 +314,24 @@ class Solver:
         _check(self.lib.cd_get_eig(self.h, which, ptr(U), ptr(lam)), "cd_get_eig")
         return U, lam
 
+    def _transfer_nrhs(self, level, fine, coarse, what):
+        if level < 0 or level + 1 >= self.cd_levels():
+            raise ValueError(f"{what}: level {level} has no coarser level")
+        Nf = self.d * self.level_m(level) ** self.d
+        Nc = self.d * self.level_m(level + 1) ** self.d
+        nf, nc = int(fine.numel()), int(coarse.numel())
+        if nf < Nf or nf % Nf or nc != (nf // Nf) * Nc:
+            raise ValueError(f"{what}: fine has {nf} entries and coarse {nc}; expected nrhs * {Nf} "
+                             f"and nrhs * {Nc}")
+        return nf // Nf
+
     def cd_restrict(self, level, fine, coarse):
-        nrhs = fine.numel() // (self.d * self.level_m(level) ** self.d)
+        nrhs = self._transfer_nrhs(level, fine, coarse, "cd_restrict")
         _check(self.lib.cd_restrict(self.h, level, _dev(fine, "float64"), _dev(coarse, "float64"), nrhs),
                "cd_restrict")
 
     def cd_prolong(self, level, coarse, fine):
-        nrhs = fine.numel() // (self.d * self.level_m(level) ** self.d)
+        nrhs = self._transfer_nrhs(level, fine, coarse, "cd_prolong")
         _check(self.lib.cd_prolong(self.h, level, _dev(coarse, "float64"), _dev(fine, "float64"), nrhs),
                "cd_prolong")
 
@@ -325,6 +367,8 @@ class Server:
     def submit(self, d, p, n, alphas, betas, b):
         b = np.ascontiguousarray(b, dtype=np.float64)
         N = cd_dofs(d, p, n)
+        if N == 0 or b.size < N or b.size % N:
+            raise ValueError(f"submit: b must hold nrhs * {N} entries (nrhs >= 1), got {b.size}")
         nrhs = b.size // N
         a = np.ascontiguousarray(np.broadcast_to(np.asarray(alphas, dtype=np.float64), (nrhs,)))
         be = np.ascontiguousarray(np.broadcast_to(np.asarray(betas, dtype=np.float64), (nrhs,)))

@@ -52,3 +52,36 @@ def test_host_side_argument_checks(lib):
     bad = c.default_options(max_batch=0)
     assert lib.cd_create(ctypes.byref(h), 2, 2, 16, 1.0, 1.0, ctypes.byref(bad), None) == c.CD_EINVAL
     assert lib.cd_strerror(c.CD_NOT_CONVERGED) == b"not converged"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of cd_options, cd_result and the server structs have the header's
+    sizes and field offsets (compiled with the host C compiler, no GPU)."""
+    import shutil
+    import subprocess
+    from paper_1805_10058_gb300 import curldiv as c
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"cd_options": c.Options, "cd_result": c.Result,
+               "cd_server_options": c.ServerOptions, "cd_server_stats": c.ServerStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "curldiv.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            a, b, v = line.split()
+            got[(a, b)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert got[(name, fname)] == getattr(cls, fname).offset, (name, fname)
