@@ -84,8 +84,17 @@ enum { CD_PREC_FP64 = 0, CD_PREC_FP32_IR = 1 };
  *   smoother; the outer Krylov method is then flexible CG.
  * CD_PC_T_BAND: the same T^{-1} as CD_PC_FD_T, by banded Cholesky solves of the
  *   1D factor along every axis (Section 6.1 applies T by banded factorisation):
- *   O(N p) work per application instead of O(N m); p <= 6. */
-enum { CD_PC_NONE = 0, CD_PC_FD_D = 1, CD_PC_FD_T = 2, CD_PC_MG = 3, CD_PC_T_BAND = 4 };
+ *   O(N p) work per application instead of O(N m); p <= 6.
+ * CD_PC_MIM: P_MIM of Section 6.2, the multi-iterative method as the preconditioner of
+ *   (flexible) CG: two V-cycles from zero per application, each with the parallel smoother on
+ *   every level and, at the finest level, p post-smoothing iterations of right-preconditioned
+ *   GMRES with T (eq:kron_precond, banded solves) in place of the parallel post-smoother
+ *   (Section 6.1); p <= 6.
+ * CD_PC_WL: P_WL of Section 6.2: one V-cycle of the same multigrid applied to the block
+ *   diagonal D = blockdiag(A^(c,c)) of eq:diag (coarse levels P^T D P, coarsest D inverted),
+ *   with p PCG iterations preconditioned by T as the finest level's post-smoother; p <= 6. */
+enum { CD_PC_NONE = 0, CD_PC_FD_D = 1, CD_PC_FD_T = 2, CD_PC_MG = 3, CD_PC_T_BAND = 4,
+       CD_PC_MIM = 5, CD_PC_WL = 6 };
 
 typedef struct {
   int precision;      /* CD_PREC_*                      (default CD_PREC_FP32_IR) */

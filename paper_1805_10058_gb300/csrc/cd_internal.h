@@ -61,6 +61,9 @@ bool spd_inverse(int n, std::vector<double>& a);
 struct Coef {  // per-solve operator coefficients, device arrays of length >= B
   const double* alpha;
   const double* beta;
+  // scale of the coupling blocks gamma = alpha - beta (NULL: 1 for every solve).  0 gives the
+  // block diagonal D = blockdiag(A^(c,c)) of eq:diag with the same kernels.
+  const double* gsc = nullptr;
 };
 
 // Chebyshev smoother interval on D^{-1} A: [kChebHi lambda_max / kChebRatio, kChebHi lambda_max]

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) apply2d_kernel(int m, int P, int TR,
                                                       const T* __restrict__ w, T* __restrict__ y,
                                                       const T* __restrict__ rhs, int mode,
                                                       const double* __restrict__ alpha,
-                                                      const double* __restrict__ beta,
+                                                      const double* __restrict__ beta, const double* __restrict__ gsc,
                                                       const int* __restrict__ active,
                                                       double* __restrict__ dotp) {
   const int b = blockIdx.y;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) apply2d_kernel(int m, int P, int TR,
     sw[idx] = (row >= 0 && row < m) ? w[base + (long long)c * m * m + (long long)row * m + j] : T(0);
   }
   __syncthreads();
-  const T a = T(alpha[b]), be = T(beta[b]), g = T(alpha[b] - beta[b]);
+  const T a = T(alpha[b]), be = T(beta[b]), g = T((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
   const T* Mb = sb;
   const T* Ab = sb + m * W;
   const T* Sb = sb + 2 * m * W;
@@ -212,7 +212,7 @@ template <typename T, int P, int TR>
 __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
     int m, const T* __restrict__ bandT, Stencil<T> cs, const T* __restrict__ w,
     T* __restrict__ y, const T* __restrict__ rhs, int mode, const double* __restrict__ alpha,
-    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp,
+    const double* __restrict__ beta, const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
     Epi<T> epi) {
   constexpr int W = 2 * P + 1;
   constexpr int NC = sizeof(T) == 8 ? 2 : 4;  // outputs per thread along x_2
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
   const T* w2 = w1 + (long long)m * m;
   const int r0 = blockIdx.x * TR;
   const int rows = min(TR, m - r0);
-  const T a = T(alpha[b]), be = T(beta[b]), g = T(alpha[b] - beta[b]);
+  const T a = T(alpha[b]), be = T(beta[b]), g = T((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
   const T* BM = bandT;
   const T* BA = bandT + (size_t)W * m;
   const T* BS = bandT + (size_t)2 * W * m;
@@ -377,7 +377,7 @@ template <typename T, int P, int TR>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel(
     int m, const T* __restrict__ bandT, Stencil<T> cs, const T* __restrict__ w,
     T* __restrict__ y, const T* __restrict__ rhs, int mode, const double* __restrict__ alpha,
-    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp,
+    const double* __restrict__ beta, const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
     Epi<T> epi) {
   using T2 = typename Pair<T>::type;
   constexpr int W = 2 * P + 1;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel
   const T* w2 = w1 + (long long)m * m;
   const int c0 = blockIdx.x * TC, r0 = blockIdx.y * TR;
   const int rows = min(TR, m - r0), cols = min(TC, m - c0);
-  const T al = T(alpha[b]), be = T(beta[b]), ga = T(alpha[b] - beta[b]);
+  const T al = T(alpha[b]), be = T(beta[b]), ga = T((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
   const T* BM = bandT;
   const T* BA = bandT + (size_t)W * m;
   const T* BS = bandT + (size_t)2 * W * m;
@@ -563,7 +563,7 @@ static void launch_v2(int m, const T* bands, const StencilHost& sh, const T* w, 
   const size_t smem = sizeof(T) * ((size_t)6 * TR * (m + 2 * P) + 8);
   dim3 grid((m + TR - 1) / TR, B);
   apply2d_v2_kernel<T, P, TR><<<grid, 256, smem, s>>>(m, bands + (size_t)3 * m * (2 * P + 1), cs,
-                                                     w, y, rhs, mode, c.alpha, c.beta, active, dotp,
+                                                     w, y, rhs, mode, c.alpha, c.beta, c.gsc, active, dotp,
                                                      g_epi<T>);
   count_launch();
   if (nblk) *nblk = grid.x;
@@ -581,7 +581,7 @@ static void launch_v3(int m, const T* bands, const StencilHost& sh, const T* w, 
   const size_t smem = (size_t)3 * (TR + 2 * P) * 64 * 2 * sizeof(T);
   dim3 grid((m + 63) / 64, (m + TR - 1) / TR, B);
   apply2d_v3_kernel<T, P, TR><<<grid, 128, smem, s>>>(m, bands + (size_t)3 * m * (2 * P + 1), cs,
-                                                     w, y, rhs, mode, c.alpha, c.beta, active, dotp,
+                                                     w, y, rhs, mode, c.alpha, c.beta, c.gsc, active, dotp,
                                                      g_epi<T>);
   count_launch();
   if (nblk) *nblk = grid.x * grid.y;
@@ -718,7 +718,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) axis_pass_kernel(AxisParams<T> prm, int d, int m, int P,
                                                         int axis, const T* __restrict__ bands,
                                                         const double* __restrict__ alpha,
-                                                        const double* __restrict__ beta,
+                                                        const double* __restrict__ beta, const double* __restrict__ gsc,
                                                         const int* __restrict__ active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(256) axis_pass_kernel(AxisParams<T> prm, int d
   long long stride = 1;
   for (int l = axis + 1; l < d; ++l) stride *= m;
   const int W = 2 * P + 1;
-  const T cf[4] = {T(1), T(alpha[b]), T(beta[b]), T(alpha[b] - beta[b])};
+  const T cf[4] = {T(1), T(alpha[b]), T(beta[b]), T((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0))};
   for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < npts;
        pt += (long long)gridDim.x * blockDim.x) {
     const int ia = (int)((pt / stride) % m);
@@ -775,7 +775,7 @@ static int apply3d_multipass(int m, int P, const T* bands, const T* w, T* y, int
       a.nt[o] = 1;
       a.t[o][0] = AxisTerm{comp, X, 0};
     }
-  axis_pass_kernel<T><<<grid, threads, 0, s>>>(a, 3, m, P, 2, bands, c.alpha, c.beta, active);
+  axis_pass_kernel<T><<<grid, threads, 0, s>>>(a, 3, m, P, 2, bands, c.alpha, c.beta, c.gsc, active);
   // pass 2: axis 1 (x_2).  Inputs: T arrays (index X*3 + comp).
   AxisParams<T> q{};
   for (int i = 0; i < 9; ++i) {
@@ -805,7 +805,7 @@ static int apply3d_multipass(int m, int P, const T* bands, const T* w, T* y, int
   q.nt[7] = 1; q.t[7][0] = {TI(M_, 2), M_, al};
   q.nt[8] = 1; q.t[8][0] = {TI(A_, 0), M_, ga};
   (void)one;
-  axis_pass_kernel<T><<<grid, threads, 0, s>>>(q, 3, m, P, 1, bands, c.alpha, c.beta, active);
+  axis_pass_kernel<T><<<grid, threads, 0, s>>>(q, 3, m, P, 1, bands, c.alpha, c.beta, c.gsc, active);
   // pass 3: axis 0 (x_1): y_c = M1 P_cM + S1 P_cS + A1 P_cA
   AxisParams<T> r{};
   for (int i = 0; i < 9; ++i) {
@@ -821,7 +821,7 @@ static int apply3d_multipass(int m, int P, const T* bands, const T* w, T* y, int
     r.t[comp][1] = {comp * 3 + 1, S_, 0};
     r.t[comp][2] = {comp * 3 + 2, A_, 0};
   }
-  axis_pass_kernel<T><<<grid, threads, 0, s>>>(r, 3, m, P, 0, bands, c.alpha, c.beta, active);
+  axis_pass_kernel<T><<<grid, threads, 0, s>>>(r, 3, m, P, 0, bands, c.alpha, c.beta, c.gsc, active);
   count_launch(3);
   return 0;
 }
@@ -849,7 +849,7 @@ template <typename T, int P, int T2>
 __global__ void __launch_bounds__(32 * T2, 2) apply3d_stream_kernel(
     int m, int L, const T* __restrict__ bandT, Stencil<T> cs, const T* __restrict__ w,
     T* __restrict__ y, const T* __restrict__ rhs, int mode, const double* __restrict__ alpha,
-    const double* __restrict__ beta, const int* __restrict__ active, double* __restrict__ dotp,
+    const double* __restrict__ beta, const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
     Epi<T> epi) {
   constexpr int W = 2 * P + 1, T3 = 32;
   constexpr int HR = T2 + 2 * P, HC = T3 + 2 * P;
@@ -866,7 +866,7 @@ __global__ void __launch_bounds__(32 * T2, 2) apply3d_stream_kernel(
   const int i2 = i2_0 + row, i3 = i3_0 + lane;
   const bool mine = i2 < m && i3 < m;
   const int k_lo = chunk * L, k_hi = min(m, k_lo + L);
-  const T al = T(alpha[b]), be = T(beta[b]), ga = T(alpha[b] - beta[b]);
+  const T al = T(alpha[b]), be = T(beta[b]), ga = T((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
   const T* BX[3] = {bandT, bandT + (size_t)W * m, bandT + (size_t)2 * W * m};
   T ec1 = 0, ec2 = 0;
   if (mode == 2) {
@@ -1036,7 +1036,7 @@ static void launch_stream3d(int m, const T* bands, const StencilHost& sh, const 
   const int nchunk = (m + L - 1) / L;
   dim3 grid((m + 31) / 32, (m + 7) / 8, nchunk * B);
   apply3d_stream_kernel<T, P, 8><<<grid, 256, stream3d_smem<T, P>(), s>>>(
-      m, L, bands + (size_t)3 * m * (2 * P + 1), cs, w, y, rhs, mode, c.alpha, c.beta, active,
+      m, L, bands + (size_t)3 * m * (2 * P + 1), cs, w, y, rhs, mode, c.alpha, c.beta, c.gsc, active,
       dotp, epi);
   count_launch();
   if (nblk) *nblk = grid.x * grid.y * nchunk;
@@ -1233,7 +1233,7 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
     size_t sm = apply2d_smem<T>(m, P, TR);
     if (sm > kApplySmemCap || (dotp && (m + TR - 1) / TR > kMaxPartials)) return 1;  // too large for v1
     dim3 grid((m + TR - 1) / TR, B);
-    apply2d_kernel<T><<<grid, 256, sm, s>>>(m, P, TR, bands, w, y, rhs, mode, c.alpha, c.beta,
+    apply2d_kernel<T><<<grid, 256, sm, s>>>(m, P, TR, bands, w, y, rhs, mode, c.alpha, c.beta, c.gsc,
                                             active, dotp);
     count_launch();
     if (nblk) *nblk = grid.x;

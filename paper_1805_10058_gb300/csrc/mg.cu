@@ -436,6 +436,12 @@ cd_status mg_set_params(MgData& mg, int d, int P, int nrhs, const std::vector<do
   std::vector<float> inv32(inv64.size());
   for (int b = 0; b < nrhs; ++b) {
     std::vector<double> D = dense_operator(d, mg.hM[L - 1], mg.hA[L - 1], mg.hS[L - 1], alpha[b], beta[b]);
+    if (mg.diag_only) {  // keep the diagonal blocks of the component-major ordering
+      const int per = nc / d;
+      for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < nc; ++j)
+          if (i / per != j / per) D[(size_t)i * nc + j] = 0.0;
+    }
     if (!spd_inverse(nc, D)) {
       set_error("coarsest multigrid matrix is not SPD");
       return CD_BREAKDOWN;
@@ -481,6 +487,7 @@ static void mg_power(MgData& mg, int B, Coef c, double* fine_scratch64, cudaStre
 }
 
 cd_status mg_prepare(MgData& mg, int B, Coef c, double* fine_scratch64, cudaStream_t s) {
+  if (mg.diag_only) c.gsc = mg.gsc_zero;
   mg_power(mg, B, c, fine_scratch64, s);
   CD_CUDA_OK(cudaGetLastError());
   return CD_OK;
@@ -549,7 +556,7 @@ static void smooth_post_fused(MgData& mg, int l, int B, const T* bl, const T* XB
 
 template <typename T>
 static void vcycle_rec(MgData& mg, int l, int B, const T* bl, T* xl, Coef c, const int* active,
-                       T* fine_scr, cudaStream_t s) {
+                       T* fine_scr, cudaStream_t s, int post) {
   T* scr = l == 0 ? fine_scr : level_scratch<T>(mg);
   if (l == mg.L - 1) {
     coarse_solve_kernel<T><<<B, 128, 0, s>>>(mg.nc, sizeof(T) == 8 ? (const T*)mg.cinv64 : (const T*)mg.cinv32,
@@ -570,9 +577,13 @@ static void vcycle_rec(MgData& mg, int l, int B, const T* bl, T* xl, Coef c, con
   launch_apply<T>(mg.d, mg.ml[l], mg.P, level_bands<T>(mg, l), cur, (T*)lb.r, bl, 1, B, c, nullptr,
                   nullptr, active, scr, s);
   mg_restrict<T>(mg.d, mg.ml[l], mg.ml[l + 1], B, (const T*)lb.r, (T*)nb.b, active, s);
-  vcycle_rec<T>(mg, l + 1, B, (const T*)nb.b, (T*)nb.x, c, active, fine_scr, s);
+  vcycle_rec<T>(mg, l + 1, B, (const T*)nb.b, (T*)nb.x, c, active, fine_scr, s, kPostCheb);
   mg_prolong_add<T>(mg.d, mg.ml[l], mg.ml[l + 1], B, (const T*)nb.x, cur, active, s);
-  if (fused) {
+  if (l == 0 && post == kPostPgmres) {
+    ks_pgmres<T>(mg, B, bl, cur, xl, c, active, scr, s);
+  } else if (l == 0 && post == kPostPcg) {
+    ks_pcg<T>(mg, B, bl, cur, xl, c, active, scr, s);
+  } else if (fused) {
     smooth_post_fused<T>(mg, l, B, bl, cur, xl, c, active, scr, s);
   } else {
     smooth<T>(mg, l, B, bl, xl, false, c, active, scr, s);
@@ -580,15 +591,101 @@ static void vcycle_rec(MgData& mg, int l, int B, const T* bl, T* xl, Coef c, con
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) add_kernel(long long N, T* __restrict__ z,
+                                                  const T* __restrict__ e,
+                                                  const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const long long base = (long long)b * N;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    z[base + i] += e[base + i];
+}
+
+template <typename T>
 void mg_vcycle(MgData& mg, int d, int P, int B, const T* r, T* z, Coef c, const int* active,
-               cudaStream_t s, T* fine_scr) {
+               cudaStream_t s, T* fine_scr, int post, int cycles) {
   (void)d;
   (void)P;
-  vcycle_rec<T>(mg, 0, B, r, z, c, active, fine_scr, s);
+  if (mg.diag_only) c.gsc = mg.gsc_zero;
+  if (post != kPostCheb && mg.ks_steps < 1) post = kPostCheb;
+  vcycle_rec<T>(mg, 0, B, r, z, c, active, fine_scr, s, post);
+  if (cycles < 2) return;
+  const long long N = mg.Nl[0];
+  T* rc = (T*)(sizeof(T) == 8 ? mg.cyc64 : mg.cyc32);
+  T* e = rc + N * (long long)mg.B;
+  for (int k = 1; k < cycles; ++k) {
+    launch_apply<T>(mg.d, mg.ml[0], mg.P, level_bands<T>(mg, 0), z, rc, r, 1, B, c, nullptr,
+                    nullptr, active, fine_scr, s);
+    vcycle_rec<T>(mg, 0, B, rc, e, c, active, fine_scr, s, post);
+    add_kernel<T><<<grid_for(N, B), 256, 0, s>>>(N, z, e, active);
+    count_launch();
+  }
 }
+
+cd_status mg_setup_ksmooth(MgData& mg, int steps, const void* Lb64, const void* dinv64,
+                           const void* Lb32, const void* dinv32) {
+  if (steps < 1 || steps > 7) {
+    set_error("Krylov post-smoother: 1 <= steps <= 7");
+    return CD_EINVAL;
+  }
+  mg.tLb64 = Lb64;
+  mg.tdinv64 = dinv64;
+  mg.tLb32 = Lb32;
+  mg.tdinv32 = dinv32;
+  if (mg.ks_steps >= steps) return CD_OK;
+  const size_t n = (size_t)mg.Nl[0] * mg.B;
+  const size_t nv = 2 * (size_t)steps + 2;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+    mg.owned.push_back(p);
+    return p;
+  };
+  mg.ks64 = alloc(nv * n * 8);
+  mg.ks32 = alloc(nv * n * 4);
+  if (!mg.cyc64) {
+    mg.cyc64 = alloc(2 * n * 8);
+    mg.cyc32 = alloc(2 * n * 4);
+  }
+  const size_t B = mg.B;
+  mg.ks_H = (double*)alloc(8 * B * (steps + 1) * steps);
+  mg.ks_hc = (double*)alloc(8 * B * 8);
+  mg.ks_y = (double*)alloc(8 * B * 8);
+  mg.ks_inv = (double*)alloc(8 * B);
+  mg.ks_beta0 = (double*)alloc(8 * B);
+  mg.ks_rz = (double*)alloc(8 * B);
+  mg.ks_a = (double*)alloc(8 * B);
+  mg.ks_b = (double*)alloc(8 * B);
+  mg.ks_part = (double*)alloc(8 * B * 8 * 256);
+  if (!mg.ks64 || !mg.ks32 || !mg.cyc64 || !mg.cyc32 || !mg.ks_H || !mg.ks_hc || !mg.ks_y ||
+      !mg.ks_inv || !mg.ks_beta0 || !mg.ks_rz || !mg.ks_a || !mg.ks_b || !mg.ks_part) {
+    cudaGetLastError();
+    set_error("Krylov post-smoother: workspace allocation failed");
+    return CD_ENOMEM;
+  }
+  mg.ks_steps = steps;
+  return CD_OK;
+}
+
+cd_status mg_set_block_diagonal(MgData& mg) {
+  if (!mg.gsc_zero) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, 8 * (size_t)std::max(1, mg.B)) != cudaSuccess) {
+      cudaGetLastError();
+      return CD_ENOMEM;
+    }
+    mg.owned.push_back(p);
+    CD_CUDA_OK(cudaMemset(p, 0, 8 * (size_t)std::max(1, mg.B)));
+    mg.gsc_zero = (double*)p;
+  }
+  mg.diag_only = true;
+  return CD_OK;
+}
+
 template void mg_vcycle<double>(MgData&, int, int, int, const double*, double*, Coef, const int*,
-                                cudaStream_t, double*);
+                                cudaStream_t, double*, int, int);
 template void mg_vcycle<float>(MgData&, int, int, int, const float*, float*, Coef, const int*,
-                               cudaStream_t, float*);
+                               cudaStream_t, float*, int, int);
 
 }  // namespace cd

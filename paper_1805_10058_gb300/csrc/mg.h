@@ -38,6 +38,19 @@ struct MgData {
   double* part = nullptr;     // partial sums [B][1024]
   double* tmpB = nullptr;     // [B]
   double alpha_cache_ok = 0;
+  // Krylov post-smoother of the finest level (Section 6.1), set up by mg_setup_ksmooth:
+  // ks_steps iterations; vectors (2 ks_steps + 2 of [B][N_0] per precision), per-solve scalars
+  int ks_steps = 0;
+  void* ks64 = nullptr;
+  void* ks32 = nullptr;
+  double *ks_H = nullptr, *ks_hc = nullptr, *ks_inv = nullptr, *ks_beta0 = nullptr, *ks_y = nullptr;
+  double *ks_part = nullptr, *ks_rz = nullptr, *ks_a = nullptr, *ks_b = nullptr;
+  const void *tLb64 = nullptr, *tLb32 = nullptr, *tdinv64 = nullptr, *tdinv32 = nullptr;  // T factor
+  // second and later V-cycles of one preconditioner application: residual and correction
+  void *cyc64 = nullptr, *cyc32 = nullptr;
+  // hierarchy of the block diagonal D of eq:diag (P_WL): coupling blocks scaled by zero
+  bool diag_only = false;
+  double* gsc_zero = nullptr;
   ~MgData();
 };
 
@@ -51,10 +64,28 @@ cd_status mg_set_params(MgData& mg, int d, int P, int nrhs, const std::vector<do
 // Computes the Chebyshev bounds (power iteration on D^{-1} A_l, FP64) for the current
 // per-solve parameters; must follow mg_set_params and the upload of alpha / beta.
 cd_status mg_prepare(MgData& mg, int B, Coef c, double* fine_scratch64, cudaStream_t s);
-// z = one V-cycle applied to r, from a zero initial guess.
+// Finest-level post-smoothing of a V-cycle: Chebyshev (the parallel smoother of every level),
+// or `steps` iterations of PGMRES / PCG preconditioned by T (Section 6.1, Section 6.2).
+enum { kPostCheb = 0, kPostPgmres = 1, kPostPcg = 2 };
+// Allocates the Krylov smoother's vectors and scalars (once) and records the banded factor of T
+// (Lb, dinv in FP64 and FP32, as for launch_tband).
+cd_status mg_setup_ksmooth(MgData& mg, int steps, const void* Lb64, const void* dinv64,
+                           const void* Lb32, const void* dinv32);
+// Turns the hierarchy into that of D = blockdiag(A^(c,c)) (eq:diag): every operator apply of the
+// multigrid runs with the coupling blocks scaled by zero; call before mg_set_params.
+cd_status mg_set_block_diagonal(MgData& mg);
+// z = `cycles` V-cycles on A z = r from z = 0 (each later cycle corrects with the residual of
+// the previous one); `post` selects the finest level's post-smoother.
 template <typename T>
 void mg_vcycle(MgData& mg, int d, int P, int B, const T* r, T* z, Coef c, const int* active,
-               cudaStream_t s, T* fine_scr);
+               cudaStream_t s, T* fine_scr, int post = kPostCheb, int cycles = 1);
+// the Krylov smoothers themselves (ksmooth.cu): xout = xin + ks_steps iterations on A x = b
+template <typename T>
+void ks_pgmres(MgData& mg, int B, const T* b, const T* xin, T* xout, Coef c, const int* active,
+               T* scr, cudaStream_t s);
+template <typename T>
+void ks_pcg(MgData& mg, int B, const T* b, const T* xin, T* xout, Coef c, const int* active,
+            T* scr, cudaStream_t s);
 template <typename T>
 void mg_restrict(int d, int mf, int mc, int B, const T* fine, T* coarse, const int* active,
                  cudaStream_t s);

@@ -95,6 +95,9 @@ struct cd_solver_s {
   int* h_cnt = nullptr;  // pinned
   MgData mg;
   std::vector<double> mg_alpha, mg_beta;  // parameters the multigrid data was prepared for
+  MgData mgD;                               // hierarchy of the block diagonal D (P_WL)
+  bool have_mgD = false;
+  std::vector<double> mgD_alpha, mgD_beta;
   std::vector<double> dev_alpha, dev_beta;  // host mirror of the per-solve alpha, beta on the device
   // CUDA graphs of a chunk of PCG iterations, keyed by (f32, B, pc, flexible, tol, maxit)
   std::map<std::tuple<int, int, int, int, int, int>, std::pair<cudaGraphExec_t, uint64_t>> graphs;
@@ -166,6 +169,16 @@ static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* 
   }
   if (pc == CD_PC_MG) {
     mg_vcycle<T>(h->mg, h->d, h->P, B, r, z, coef_of(h), active, h->s, w.apply_scratch.as<T>());
+    return;
+  }
+  if (pc == CD_PC_MIM) {  // P_MIM: two V-cycles, PGMRES-T post-smoothing on the finest level
+    mg_vcycle<T>(h->mg, h->d, h->P, B, r, z, coef_of(h), active, h->s, w.apply_scratch.as<T>(),
+                 kPostPgmres, 2);
+    return;
+  }
+  if (pc == CD_PC_WL) {  // P_WL: one V-cycle on D, PCG-T post-smoothing on the finest level
+    mg_vcycle<T>(h->mgD, h->d, h->P, B, r, z, coef_of(h), active, h->s, w.apply_scratch.as<T>(),
+                 kPostPcg, 1);
     return;
   }
   if (pc == CD_PC_T_BAND) {
@@ -248,7 +261,7 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
   // a Krylov-smoothed / multigrid or tensor-core (TF32) preconditioner is not an exactly
   // fixed symmetric operator: use the flexible update there
   const int flexible =
-      (pc == CD_PC_MG ||
+      (pc == CD_PC_MG || pc == CD_PC_MIM || pc == CD_PC_WL ||
        (sizeof(T) == 4 && h->opt.fd_tensor_cores && (pc == CD_PC_FD_D || pc == CD_PC_FD_T)))
           ? 1
           : 0;
@@ -365,7 +378,7 @@ static cd_status final_residual(cd_solver h, int B, const double* b, const doubl
 
 static cd_status set_params(cd_solver h, int nrhs, const double* alphas, const double* betas,
                             std::vector<double>* pa = nullptr, std::vector<double>* pb = nullptr,
-                            bool need_mg = false) {
+                            int pc_kind = -1) {
   std::vector<double> a(nrhs), b(nrhs);
   for (int i = 0; i < nrhs; ++i) {
     a[i] = alphas ? alphas[i] : h->alpha0;
@@ -393,6 +406,15 @@ static cd_status set_params(cd_solver h, int nrhs, const double* alphas, const d
   }
   if (pa) *pa = a;
   if (pb) *pb = b;
+  if (pc_kind == CD_PC_WL && (a != h->mgD_alpha || b != h->mgD_beta)) {
+    cd_status st = mg_set_params(h->mgD, h->d, h->P, nrhs, a, b, h->s);
+    if (st != CD_OK) return st;
+    st = mg_prepare(h->mgD, nrhs, coef_of(h), h->w64.apply_scratch.as<double>(), h->s);
+    if (st != CD_OK) return st;
+    h->mgD_alpha = a;
+    h->mgD_beta = b;
+  }
+  const bool need_mg = pc_kind == CD_PC_MG || pc_kind == CD_PC_MIM;
   if (need_mg && (a != h->mg_alpha || b != h->mg_beta)) {
     cd_status st = mg_set_params(h->mg, h->d, h->P, nrhs, a, b, h->s);
     if (st != CD_OK) return st;
@@ -599,6 +621,11 @@ size_t solver_bytes(int d, int p, int n, const cd_options& opt) {
   if (d == 3) bytes += 21 * n3_1 * B * 12;
   if (opt.precond == CD_PC_FD_D || opt.precond == CD_PC_FD_T)
     bytes += (size_t)m * m * 12 * 4;
+  if (opt.precond == CD_PC_MIM || opt.precond == CD_PC_WL) {
+    bytes += B * N * (2 * (size_t)p + 4) * 12;  // Krylov smoother and cycle vectors
+    if (opt.precond == CD_PC_WL)                 // the second (block-diagonal) hierarchy
+      bytes += (size_t)(6 * 12 * (double)B * N * (d == 2 ? 4.0 / 3.0 : 8.0 / 7.0));
+  }
   if (opt.ext_residual) {
     const size_t per = (size_t)6 * N;  // residual intermediates (hi, lo) per solve, doubles
     bytes += 8 * B * N + 8 * std::min(B * per, std::max(per, (size_t)(256u << 20) / 8));
@@ -656,6 +683,7 @@ const char* cd_last_error(void) { return cd::last_error(); }
 uint64_t cd_kernel_launches(void) { return cd::launches(); }
 
 static cd_status ensure_tband(cd_solver h);
+static cd_status ensure_ksmooth(cd_solver h, int kind);
 
 cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double beta,
                     const cd_options* opt, void* stream) {
@@ -680,7 +708,7 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   cd_default_options(&h->opt);
   if (opt) h->opt = *opt;
   if (h->opt.max_batch < 1 || h->opt.max_batch > 4096 || h->opt.chunk < 1 || h->opt.maxit < 1 ||
-      !(h->opt.rtol > 0) || h->opt.precond < 0 || h->opt.precond > CD_PC_T_BAND || h->opt.precision < 0 ||
+      !(h->opt.rtol > 0) || h->opt.precond < 0 || h->opt.precond > CD_PC_WL || h->opt.precision < 0 ||
       h->opt.precision > 1) {
     set_error("invalid options");
     return CD_EINVAL;
@@ -740,13 +768,44 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     std::vector<double> c(3 * W);
     for (int x = 0; x < 3; ++x)
       for (int k = 0; k < W; ++k) c[x * W + k] = X[x]->v[(size_t)ic * W + k];
-    central.push_back(c);
-    // The interior rows agree with the central row up to quadrature rounding; they are
-    // replaced by it, so that a kernel reading the constant stencil and one reading the band
-    // row see the same coefficients (and produce the same bits).
+    // The central row is made exactly symmetric (M, S) or antisymmetric (A), as the Toeplitz
+    // symbols of Section 3.2 are.  The interior rows agree with it up to quadrature rounding;
+    // they are replaced by it, so that a kernel reading the constant stencil and one reading the
+    // band row see the same coefficients (and produce the same bits).  Then every entry below
+    // the diagonal is set from its transpose (the interior row's value where one of the two rows
+    // is interior), so M and S stay exactly symmetric and A exactly skew: the operator
+    // gamma A (x) A of the kernels is then exactly the printed -alpha A^T (x) A + beta A (x) A^T,
+    // and the block matrix exactly symmetric.
+    for (int x = 0; x < 3; ++x)
+      for (int k = 1; k <= P; ++k) {
+        double& up = c[x * W + P + k];
+        double& dn = c[x * W + P - k];
+        const double v = x == 1 ? 0.5 * (up - dn) : 0.5 * (up + dn);
+        up = v;
+        dn = x == 1 ? -v : v;
+      }
+    c[1 * W + P] = 0.0;
     for (int i = lo; i < hi; ++i)
       for (int x = 0; x < 3; ++x)
         for (int k = 0; k < W; ++k) X[x]->v[(size_t)i * W + k] = c[x * W + k];
+    for (int x = 0; x < 3; ++x) {
+      const double sgn = x == 1 ? -1.0 : 1.0;
+      std::vector<double>& v = X[x]->v;
+      for (int i = 0; i < ml; ++i)
+        for (int k = 1; k <= P && i + k < ml; ++k) {
+          const int j = i + k;
+          const bool ii = i >= lo && i < hi, jj = j >= lo && j < hi;
+          double& upper = v[(size_t)i * W + P + k];  // X(i, j)
+          double& lower = v[(size_t)j * W + P - k];  // X(j, i)
+          if (!ii && jj)
+            upper = sgn * lower;
+          else
+            lower = sgn * upper;
+        }
+      if (x == 1)
+        for (int i = 0; i < ml; ++i) v[(size_t)i * W + P] = 0.0;
+    }
+    central.push_back(c);
     h->boff.push_back(all.size());
     for (int x = 0; x < 3; ++x) all.insert(all.end(), X[x]->v.begin(), X[x]->v.end());
     for (int x = 0; x < 3; ++x)
@@ -820,6 +879,10 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     cd_status st = mg_build(h->mg, d, P, h->ml, h->hM, h->hA, h->hS, B,
                             std::max(1, h->opt.smoother_degree), h->bands64.as<double>(),
                             h->bands32.as<float>(), h->boff);
+    if (st != CD_OK) return st;
+  }
+  if (h->opt.precond == CD_PC_MIM || h->opt.precond == CD_PC_WL) {
+    cd_status st = ensure_ksmooth(h.get(), h->opt.precond);
     if (st != CD_OK) return st;
   }
   if (h->opt.autotune && d == 2) {  // pick the 2D apply variant per level and precision
@@ -899,7 +962,7 @@ cd_status cd_solve(cd_solver h, const double* b, double* x, int nrhs, const doub
   if (st != CD_OK) return st;
   std::lock_guard<std::mutex> lk(h->mu);
   std::vector<double> va, vb;
-  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond == CD_PC_MG)) != CD_OK) return st;
+  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond)) != CD_OK) return st;
   return solve_device(h, b, x, nullptr, nrhs, res, va, vb);
 }
 
@@ -909,7 +972,7 @@ cd_status cd_solve_ext(cd_solver h, const double* b, double* x, double* x_lo, in
   if (st != CD_OK) return st;
   std::lock_guard<std::mutex> lk(h->mu);
   std::vector<double> va, vb;
-  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond == CD_PC_MG)) != CD_OK) return st;
+  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond)) != CD_OK) return st;
   return solve_device(h, b, x, x_lo, nrhs, res, va, vb);
 }
 
@@ -919,7 +982,7 @@ cd_status cd_solve_host(cd_solver h, const double* b_host, double* x_host, int n
   if (st != CD_OK) return st;
   std::lock_guard<std::mutex> lk(h->mu);
   std::vector<double> va, vb;
-  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond == CD_PC_MG)) != CD_OK) return st;
+  if ((st = set_params(h, nrhs, alphas, betas, &va, &vb, h->opt.precond)) != CD_OK) return st;
   const size_t bytes = 8 * (size_t)nrhs * h->N;
   if (!h->b64.p) {
     if (h->b64.alloc(8 * (size_t)h->Bcap * h->N) != cudaSuccess ||
@@ -956,6 +1019,24 @@ static cd_status ensure_tband(cd_solver h) {
   }
   h->have_tband = true;
   return CD_OK;
+}
+
+// The finest-level Krylov post-smoother (p iterations preconditioned by T, banded solves) of
+// P_MIM (on the hierarchy of A) or P_WL (on that of D, built here on first use).
+static cd_status ensure_ksmooth(cd_solver h, int kind) {
+  cd_status st = ensure_tband(h);
+  if (st != CD_OK) return st;
+  if (kind == CD_PC_WL && !h->have_mgD) {
+    st = mg_build(h->mgD, h->d, h->P, h->ml, h->hM, h->hA, h->hS, h->Bcap,
+                  std::max(1, h->opt.smoother_degree), h->bands64.as<double>(),
+                  h->bands32.as<float>(), h->boff);
+    if (st != CD_OK) return st;
+    st = mg_set_block_diagonal(h->mgD);
+    if (st != CD_OK) return st;
+    h->have_mgD = true;
+  }
+  MgData& mg = kind == CD_PC_WL ? h->mgD : h->mg;
+  return mg_setup_ksmooth(mg, h->p, h->TB64.p, h->TBd64.p, h->TB32.p, h->TBd32.p);
 }
 
 // ------------------------------------------------------------------ host-only set-up queries
@@ -1027,7 +1108,7 @@ cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs, co
                      const double* betas, int f32) {
   cd_status st = check_call(h, r, z, nrhs);
   if (st != CD_OK) return st;
-  if (kind < CD_PC_NONE || kind > CD_PC_T_BAND) return CD_EINVAL;
+  if (kind < CD_PC_NONE || kind > CD_PC_WL) return CD_EINVAL;
   std::lock_guard<std::mutex> lk(h->mu);
   if (kind == CD_PC_FD_D || kind == CD_PC_FD_T) {
     st = ensure_fd(h);
@@ -1037,7 +1118,11 @@ cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs, co
     st = ensure_tband(h);
     if (st != CD_OK) return st;
   }
-  st = set_params(h, nrhs, alphas, betas, nullptr, nullptr, kind == CD_PC_MG);
+  if (kind == CD_PC_MIM || kind == CD_PC_WL) {
+    st = ensure_ksmooth(h, kind);
+    if (st != CD_OK) return st;
+  }
+  st = set_params(h, nrhs, alphas, betas, nullptr, nullptr, kind);
   if (st != CD_OK) return st;
   if (f32)
     apply_prec<float>(h, kind, nrhs, (const float*)r, (float*)z, nullptr);

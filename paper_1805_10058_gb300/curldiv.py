@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libcurldiv.so")
 
 CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_NOT_CONVERGED, CD_BREAKDOWN, CD_TIMEOUT, CD_CANCELLED = range(8)
 CD_PREC_FP64, CD_PREC_FP32_IR = 0, 1
-CD_PC_NONE, CD_PC_FD_D, CD_PC_FD_T, CD_PC_MG, CD_PC_T_BAND = 0, 1, 2, 3, 4
+CD_PC_NONE, CD_PC_FD_D, CD_PC_FD_T, CD_PC_MG, CD_PC_T_BAND, CD_PC_MIM, CD_PC_WL = 0, 1, 2, 3, 4, 5, 6
 
 
 class Options(ctypes.Structure):
