@@ -241,6 +241,31 @@ CD_API cd_status cd_restrict(cd_solver h, int level, const double* fine, double*
 CD_API cd_status cd_prolong(cd_solver h, int level, const double* coarse, double* fine,
                             int nrhs);
 
+/* ---------------------------------------------------------------- spectral validation
+ * Eigenvalue functions of the d x d symbol f^{p,alpha,beta} of Theorem 5.1 (eq:f2D, d = 2) /
+ * Theorem 5.5 (eq:f3D, d = 3), sampled on the grid Gamma of Section 5.3: theta_k = k pi / mg,
+ * k = 1..mg per direction, points in C order (theta_1 slowest).  lam: device, mg^d * d doubles,
+ * the d eigenvalues of each point in ascending order (Lambda_1..Lambda_d of Section 5.3).
+ * lap: device, mg^d doubles or NULL, the Laplacian symbol (eq:lapl2D / eq:lapl3D) that bounds
+ * them, min(alpha,beta) lap <= lambda_i <= max(alpha,beta) lap (Theorems 5.2 / 5.6).
+ * nu: d host doubles (the anisotropy n_l = n nu_l of the theorems' weights gamma_i, delta_i) or
+ * NULL for nu = 1.  Stream-ordered on `cuda_stream`; nothing is allocated.  CD_EINVAL for d not
+ * in {2,3}, p outside 1..8, mg < 1, non-positive parameters or weights, lam == NULL. */
+CD_API cd_status cd_symbol_eigs(int d, int p, double alpha, double beta, const double* nu,
+                                int mg, double* lam, double* lap, void* cuda_stream);
+
+/* `steps` Lanczos steps with the handle's FP64 operator (eq:matr_Amu / eq:matr_Amu3D) from the
+ * start vectors v0 (device, nrhs right-hand-side layout, any nonzero vectors), no
+ * reorthogonalisation: lam_min / lam_max (host, nrhs) receive the extreme eigenvalues of the
+ * Lanczos tridiagonal matrix (Ritz values, inside [lambda_min(A), lambda_max(A)] and converging
+ * to them), the check of Section 5.3's spectra against the symbol bounds.  diag / offdiag (host,
+ * nrhs * steps each, or NULL) receive alpha_j and beta_{j+1}.  A solve whose Krylov space becomes
+ * invariant stops early (its remaining coefficients are zero).  CD_EINVAL for steps outside
+ * 1..4096 or the argument errors listed at the top. */
+CD_API cd_status cd_lanczos(cd_solver h, const double* v0, int nrhs, int steps,
+                            const double* alphas, const double* betas, double* lam_min,
+                            double* lam_max, double* diag, double* offdiag);
+
 /* Number of this library's kernels launched by this process so far. */
 CD_API uint64_t cd_kernel_launches(void);
 

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcurldiv.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["setup.cpp", "kernels.cu", "krylov.cu", "mg.cu", "solver.cu", "server.cpp",
-           "static_apply.cu", "fd_tc.cu", "ext_residual.cu", "ksmooth.cu"]
+           "static_apply.cu", "fd_tc.cu", "ext_residual.cu", "ksmooth.cu", "spectral.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -18,6 +18,13 @@
 
 namespace cd {
 uint64_t launches();
+int launch_symbol_eigs(int d, int p, double alpha, double beta, const double* nu, int mg,
+                       double* lam, double* lap, cudaStream_t s);
+void lanczos_run(long long N, int B, int steps, const double* v0, double* v, double* w,
+                 double* vprev, double* la, double* lb, double* coef, double* inv, int* live,
+                 int* used, double* part, void (*apply)(void*, const double*, double*), void* ctx,
+                 cudaStream_t s);
+void tridiag_extremes(const double* a, const double* b, int k, double* lmin, double* lmax);
 
 // ------------------------------------------------------------------ device buffers
 struct DevBuf {
@@ -90,6 +97,7 @@ struct cd_solver_s {
   DevBuf ir_rrprev, ir_grp, ir_tol2, ir_m0, ir_m1, ir_m2;
   DevBuf b64, x64, r64;
   DevBuf xlo64, ext_scratch;  // low parts of the double-FP64 solution; residual intermediates
+  DevBuf lz_a, lz_b;          // Lanczos tridiagonal coefficients (cd_lanczos)
   int ext_chunk = 0;          // solves per launch of the extended residual
   Workspace w64, w32;
   int* h_cnt = nullptr;  // pinned
@@ -1133,6 +1141,84 @@ cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs, co
 }
 
 int cd_levels(cd_solver h) { return h ? (int)h->ml.size() : 0; }
+
+cd_status cd_symbol_eigs(int d, int p, double alpha, double beta, const double* nu, int mg,
+                         double* lam, double* lap, void* stream) {
+  if ((d != 2 && d != 3) || p < 1 || p > 8 || mg < 1 || !lam) {
+    set_error("cd_symbol_eigs: need d in {2,3}, 1 <= p <= 8, mg >= 1, lam != NULL");
+    return CD_EINVAL;
+  }
+  if (!(alpha > 0) || !(beta > 0) || !std::isfinite(alpha) || !std::isfinite(beta)) {
+    set_error("cd_symbol_eigs: alpha and beta must be finite and > 0");
+    return CD_EINVAL;
+  }
+  if (nu)
+    for (int l = 0; l < d; ++l)
+      if (!(nu[l] > 0) || !std::isfinite(nu[l])) {
+        set_error("cd_symbol_eigs: nu must be finite and > 0");
+        return CD_EINVAL;
+      }
+  double np = 1;
+  for (int l = 0; l < d; ++l) np *= mg;
+  if (np > 4e9) {
+    set_error("cd_symbol_eigs: grid too large");
+    return CD_EINVAL;
+  }
+  launch_symbol_eigs(d, p, alpha, beta, nu, mg, lam, lap, static_cast<cudaStream_t>(stream));
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+struct LanczosCtx {
+  cd_solver h;
+  int B;
+};
+static void lanczos_apply(void* ctx, const double* x, double* y) {
+  LanczosCtx* c = static_cast<LanczosCtx*>(ctx);
+  apply_level<double>(c->h, 0, x, y, nullptr, 0, c->B, nullptr, nullptr, nullptr);
+}
+
+cd_status cd_lanczos(cd_solver h, const double* v0, int nrhs, int steps, const double* alphas,
+                     const double* betas, double* lam_min, double* lam_max, double* diag,
+                     double* offdiag) {
+  cd_status st = check_call(h, v0, lam_min ? (const void*)lam_min : (const void*)lam_max, nrhs);
+  if (st != CD_OK) return st;
+  if (!lam_min || !lam_max || steps < 1 || steps > 4096) {
+    set_error("cd_lanczos: need lam_min, lam_max != NULL and 1 <= steps <= 4096");
+    return CD_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(h->mu);
+  if ((st = set_params(h, nrhs, alphas, betas)) != CD_OK) return st;
+  const size_t need = 8 * (size_t)h->Bcap * steps;
+  if (h->lz_a.bytes < need) {
+    if (h->lz_a.alloc(need) != cudaSuccess || h->lz_b.alloc(need) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cd_lanczos: allocation failed");
+      return CD_ENOMEM;
+    }
+  }
+  const int B = nrhs;
+  CD_CUDA_OK(cudaMemsetAsync(h->lz_a.p, 0, need, h->s));
+  CD_CUDA_OK(cudaMemsetAsync(h->lz_b.p, 0, need, h->s));
+  LanczosCtx ctx{h, B};
+  lanczos_run(h->N, B, steps, v0, h->w64.x.as<double>(), h->w64.r.as<double>(),
+              h->w64.z.as<double>(), h->lz_a.as<double>(), h->lz_b.as<double>(),
+              h->sd[0].as<double>(), h->sd[1].as<double>(), h->si[0].as<int>(),
+              h->si[1].as<int>(), h->part[0].as<double>(), lanczos_apply, &ctx, h->s);
+  std::vector<double> a((size_t)B * steps), b((size_t)B * steps);
+  std::vector<int> used(B);
+  CD_CUDA_OK(cudaMemcpyAsync(a.data(), h->lz_a.p, a.size() * 8, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(b.data(), h->lz_b.p, b.size() * 8, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(used.data(), h->si[1].p, B * 4, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaStreamSynchronize(h->s));
+  for (int i = 0; i < B; ++i) {
+    const int k = std::max(1, std::min(steps, used[i]));
+    tridiag_extremes(&a[(size_t)i * steps], &b[(size_t)i * steps], k, &lam_min[i], &lam_max[i]);
+  }
+  if (diag) std::memcpy(diag, a.data(), a.size() * 8);
+  if (offdiag) std::memcpy(offdiag, b.data(), b.size() * 8);
+  return CD_OK;
+}
 
 cd_status cd_get_bands(cd_solver h, int level, double* M, double* A, double* S, int* m_out,
                        int* P_out) {

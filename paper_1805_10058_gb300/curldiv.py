@@ -91,6 +91,8 @@ def load(path=LIB_PATH):
         "cd_restrict": (i, [vp, i, vp, vp, i]),
         "cd_prolong": (i, [vp, i, vp, vp, i]),
         "cd_kernel_launches": (ctypes.c_uint64, []),
+        "cd_symbol_eigs": (i, [i, i, d, d, dp, i, vp, vp, vp]),
+        "cd_lanczos": (i, [vp, vp, i, i, dp, dp, dp, dp, dp, dp]),
         "cd_apply3d_static": (i, [i, i, d, d, vp, vp, i, vp]),
         "cd_setup_bands": (i, [i, i, i, dp, dp, dp, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "cd_setup_eig": (i, [i, i, i, dp, dp]),
@@ -190,6 +192,23 @@ def _nrhs(N, a, b, what):
         raise ValueError(f"{what}: expected two vectors of the same length nrhs * {N} (nrhs >= 1), "
                          f"got {na} and {nb} entries")
     return na // N
+
+
+def cd_symbol_eigs(d, p, alpha, beta, mg, lam, lap=None, nu=None, stream=None):
+    """Eigenvalues of the symbol on the grid Gamma (device tensors lam [mg^d * d], lap [mg^d])."""
+    import torch
+    npts = mg ** d
+    if lam.numel() != npts * d or (lap is not None and lap.numel() != npts):
+        raise ValueError(f"cd_symbol_eigs: lam needs {npts * d} entries and lap {npts}")
+    nuv = None if nu is None else np.ascontiguousarray(np.asarray(nu, dtype=np.float64))
+    if nuv is not None and nuv.size != d:
+        raise ValueError("cd_symbol_eigs: nu needs d entries")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    st = load().cd_symbol_eigs(d, p, alpha, beta, None if nuv is None else _dp(nuv), mg,
+                               _dev(lam, "float64"), None if lap is None else _dev(lap, "float64"),
+                               ctypes.c_void_p(stream))
+    _check(st, "cd_symbol_eigs")
 
 
 def _params(nrhs, alphas, betas):
@@ -292,6 +311,16 @@ class Solver:
         dt = "float32" if f32 else "float64"
         _check(self.lib.cd_precond(self.h, kind, _dev(r, dt), _dev(z, dt), nrhs, pa, pb, int(f32)),
                "cd_precond")
+
+    def cd_lanczos(self, v0, steps, alphas=None, betas=None):
+        """Lanczos extremes of A for the start vectors v0 (FP64 CUDA tensor of nrhs * N)."""
+        nrhs = _nrhs(self.N, v0, v0, "cd_lanczos")
+        keep, pa, pb = _params(nrhs, alphas, betas)
+        lmin, lmax = np.zeros(nrhs), np.zeros(nrhs)
+        a, b = np.zeros((nrhs, steps)), np.zeros((nrhs, steps))
+        _check(self.lib.cd_lanczos(self.h, _dev(v0, "float64"), nrhs, steps, pa, pb, _dp(lmin),
+                                   _dp(lmax), _dp(a), _dp(b)), "cd_lanczos")
+        return lmin, lmax, a, b
 
     def cd_levels(self):
         return int(self.lib.cd_levels(self.h))
