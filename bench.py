@@ -2,11 +2,12 @@
 
 Workload (one step): the 2D sweep -- p in {2, 3, 4}, n = 256 (m = n + p - 2 per axis,
 2 m^2 unknowns per solve), alpha = 1, beta in {1e-6, 1e-3, 1, 1e3, 1e6}, 8 seeded
-uniform[-1, 1] right-hand sides per (p, beta): 120 solves to relative residual 1e-10,
-multigrid-preconditioned flexible CG with FP32 inner solves inside FP64 refinement
-(FP64 Krylov + FP32 multigrid for the parameter ratios 1e6).  The 40 solves of one p
-form one batched call.  All right-hand sides are resident in HBM before timing; L2 is
-flushed (256 MB write) before every timed step.
+uniform[-1, 1] right-hand sides per (p, beta): 120 solves to relative residual 1e-10 of the
+double-FP64 solution x + x_lo (cd_solve_ext), multigrid-preconditioned flexible CG with
+FP32 inner solves (FP64 inner solves at parameter ratios >= 1e4) inside a refinement loop
+whose residual is evaluated in double-FP64.  The 40 solves of one p form one batched call.
+All right-hand sides are resident in HBM before timing; L2 is flushed (256 MB write)
+before every timed step.  `value` counts the solves that reached the tolerance.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,10 +34,9 @@ N_INT = 256
 BETAS = (1e-6, 1e-3, 1.0, 1e3, 1e6)
 SEEDS = tuple(range(8))
 RTOL = 1e-10
-APPLY_KERNEL_TAG = "apply2d_v3_t64_diag_rn"  # FP32 2D apply version; traffic is read only if the committed ncu counters are for it
 WORKLOAD = ("2D curl-div sweep: p in {2,3,4}, n=256 (~131k-133k DoF/solve), alpha=1, "
             "beta in {1e-6,1e-3,1,1e3,1e6}, 8 uniform[-1,1] RHS per case (120 solves), "
-            "MG-preconditioned FCG, FP32 inner + FP64 refinement, rtol 1e-10")
+            "MG-preconditioned FCG, FP32 inner + double-FP64 refinement, rtol 1e-10")
 
 
 def peaks():
@@ -121,30 +121,50 @@ def aggregate(total_ms, solves_local, ws, device=None):
 
 
 # ------------------------------------------------------------------ reference (oracle) arm
-# The oracle's sparse direct solve takes minutes per n = 256 system and its CG needs
-# 10^4+ iterations below beta = 1e-3, so the CPU arm times a bounded sample: the paper's
-# plain CG (oracle.solvers.cg, FP64) at beta = 1, one right-hand side, cycling over p.
-REF_SAMPLE = "oracle plain CG (FP64, Section 6.2 CG) to rtol 1e-10 at beta=1, one uniform RHS per solve, cycling p in {2,3,4}; the easiest case of the sweep"
+# The oracle's sparse direct solve takes minutes per n = 256 system and its Krylov solves need
+# 10^3-10^4 iterations away from beta = 1, so the CPU legs time a bounded sample of the sweep:
+# the oracle's P_MIM (Section 6.2, the paper's best strategy: CG preconditioned by two V-cycles
+# with symmetric Gauss-Seidel and PGMRES-T post-smoothing) at beta = 1, p = 2, n = 256, one
+# uniform right-hand side per solve, rtol 1e-10, one solve per host core in spawned processes.
+REF_P = 2
+REF_SAMPLE = ("oracle P_MIM (FP64, Section 6.2) to rtol 1e-10 at beta=1, p=2, n=256, one uniform RHS "
+              "per solve, one solve per host core")
 
 
-def oracle_solve(p, seed):
+def host_cores():
+    """CPUs this process may run on (at most 16 worker processes)."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    return max(1, min(n, 16))
+
+
+def oracle_job(args):
+    """One oracle solve: returns (setup s, solve s, iterations, DoF).  Setup = assembly of A
+    and of the multigrid hierarchy; solve = the preconditioned CG iterations."""
+    p, seed, method = args
     from oracle import assemble, solvers
     from paper_1805_10058_gb300 import inputs
+    t0 = time.perf_counter()
     b = inputs.uniform_rhs(2, p, N_INT, seed=seed)[0]
     A = assemble.galerkin_kron(2, p, N_INT, 1.0, 1.0)
-    x, k, _ = solvers.cg(A, b, RTOL, 100000)
+    prec = solvers.mim_preconditioner(A, 2, p, N_INT + p - 2) if method == "pmim" else None
+    t1 = time.perf_counter()
+    x, k, _ = solvers.cg(A, b, RTOL, 100000, prec, flexible=prec is not None)
+    t2 = time.perf_counter()
     rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
     assert rel <= 1.01 * RTOL, rel
-    return k
+    return t1 - t0, t2 - t1, k, b.size
 
 
-def _parallel_oracle_steps(nsteps, warmup):
-    """Times nsteps steps of one oracle solve per host core (spawned processes, one thread
-    each) after `warmup` untimed steps; returns (cores, [step seconds]) or None when the pool
-    cannot run here."""
+def _pool_rounds(nrounds, warmup, method, p=REF_P):
+    """Times rounds of one oracle solve per host core (spawned single-threaded processes: the
+    caller may have initialised CUDA).  Returns (cores, [round seconds], [job results]) or None
+    when no process pool can run here."""
     import concurrent.futures as cf
     import multiprocessing as mp
-    cores = max(1, min(os.cpu_count() or 1, 16))
+    cores = host_cores()
     if cores == 1:
         return None
     old = os.environ.get("OMP_NUM_THREADS")
@@ -152,15 +172,16 @@ def _parallel_oracle_steps(nsteps, warmup):
     ex = None
     try:
         ex = cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
-        times = []
-        for it in range(warmup + nsteps):
-            jobs = [(PS[(it * cores + k) % len(PS)], 1000 * it + k) for k in range(cores)]
+        times, jobs_out = [], []
+        for it in range(warmup + nrounds):
+            jobs = [(p, 1000 * it + k, method) for k in range(cores)]
             t0 = time.perf_counter()
-            list(ex.map(_oracle_solve_job, jobs, timeout=600))
+            res = list(ex.map(oracle_job, jobs, timeout=900))
             if it >= warmup:
                 times.append(time.perf_counter() - t0)
+                jobs_out.extend(res)
         ex.shutdown(wait=True)
-        return cores, times
+        return cores, times, jobs_out
     except Exception:
         if ex is not None:  # stop this pool's own workers without waiting on them
             procs = list(getattr(ex, "_processes", {}).values())
@@ -179,20 +200,19 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    par = _parallel_oracle_steps(args.steps, args.warmup)
+    par = _pool_rounds(args.steps, args.warmup, "pmim")
     if par is not None:
-        cores, times = par
+        cores, times, jobs = par
         nsolves = cores * len(times)
-        sample = f"{len(times)} steps of {cores} solves, one per host core: {REF_SAMPLE}"
+        sample = f"{len(times)} steps of {cores} solves: {REF_SAMPLE}"
     else:  # one core, one solve per step
-        cores, times = 1, []
+        cores, times, jobs = 1, [], []
         for it in range(args.warmup + args.steps):
-            p = PS[it % len(PS)]
             t0 = time.perf_counter()
-            oracle_solve(p, seed=it)
-            dt = time.perf_counter() - t0
+            r = oracle_job((REF_P, it, "pmim"))
             if it >= args.warmup:
-                times.append(dt)
+                times.append(time.perf_counter() - t0)
+                jobs.append(r)
         nsolves = len(times)
         sample = f"{len(times)} solves on one core: {REF_SAMPLE}"
     tot = sum(times)
@@ -202,62 +222,163 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "step": REF_SAMPLE},
             "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample,
+                             "setup_s_median": float(np.median([j[0] for j in jobs])),
+                             "solve_s_median": float(np.median([j[1] for j in jobs]))},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def _oracle_solve_job(args):
-    p, seed = args
-    return oracle_solve(p, seed)
-
-
 def cpu_baseline_sample():
-    """The oracle as it stands on a bounded sample: one solve per host core in parallel
-    processes (spawned: the caller has initialised CUDA), plus a one-core run of two solves."""
-    import concurrent.futures as cf
-    import multiprocessing as mp
-    t0 = time.perf_counter()
-    for p in (2, 3):
-        oracle_solve(p, seed=1)
-    dt1 = time.perf_counter() - t0
-    one_core = {"value": 2 / dt1, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                "sample": f"2 solves (p=2,3) on one core in {dt1:.1f} s: {REF_SAMPLE}"}
-    cores = max(1, min(os.cpu_count() or 1, 16))
-    if cores == 1:
-        return one_core
-    jobs = [(PS[k % 2], 100 + k) for k in range(cores)]
-    old = os.environ.get("OMP_NUM_THREADS")
-    os.environ["OMP_NUM_THREADS"] = "1"  # one thread per process
-    ex = None
-    try:
-        ex = cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
-        list(ex.map(_oracle_solve_job, jobs[:1], timeout=300))  # start-up outside the timing
-        t0 = time.perf_counter()
-        list(ex.map(_oracle_solve_job, jobs, timeout=300))
-        dtn = time.perf_counter() - t0
-        ex.shutdown(wait=True)
-    except Exception as exc:  # the pool could not run here: report the one-core sample
-        if ex is not None:  # stop this pool's own workers without waiting on them
-            procs = list(getattr(ex, "_processes", {}).values())
-            ex.shutdown(wait=False, cancel_futures=True)
-            for pr in procs:
-                pr.kill()
-        one_core["sample"] += f" (parallel sample unavailable: {type(exc).__name__})"
-        return one_core
-    finally:
-        if old is None:
-            os.environ.pop("OMP_NUM_THREADS", None)
-        else:
-            os.environ["OMP_NUM_THREADS"] = old
-    return {"value": len(jobs) / dtn, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "value_1core": 2 / dt1,
-            "sample": f"{len(jobs)} solves (p=2,3 alternating) on {cores} processes in {dtn:.1f} s, "
-                      f"and 2 solves on one core in {dt1:.1f} s: {REF_SAMPLE}"}
+    """The oracle as it stands on a bounded sample (REF_SAMPLE): three rounds of one P_MIM solve
+    per host core (median round reported), setup and solve timed separately, DoF/s; beside it one
+    round of the oracle's plain CG on the same systems."""
+    par = _pool_rounds(3, 0, "pmim")
+    cg = _pool_rounds(1, 0, "cg")
+    if par is None:  # no process pool here: one solve on one core
+        t = oracle_job((REF_P, 1, "pmim"))
+        return {"value": 1.0 / (t[0] + t[1]), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": "1 solve on one core: " + REF_SAMPLE, "setup_s_median": t[0],
+                "solve_s_median": t[1], "dof_per_s": t[3] / (t[0] + t[1])}
+    cores, times, jobs = par
+    med = float(np.median(times))
+    out = {"value": cores / med, "unit": "solves/s", "cores": cores, "kind": "oracle",
+           "sample": f"median of 3 rounds of {cores} solves: {REF_SAMPLE}",
+           "round_s": times, "setup_s_median": float(np.median([j[0] for j in jobs])),
+           "solve_s_median": float(np.median([j[1] for j in jobs])),
+           "iters_median": float(np.median([j[2] for j in jobs])),
+           "dof_per_s": cores * jobs[0][3] / med}
+    if cg is not None:
+        c_cores, c_times, c_jobs = cg
+        out["plain_cg"] = {"value": c_cores / c_times[0], "unit": "solves/s",
+                           "iters_median": float(np.median([j[2] for j in c_jobs])),
+                           "sample": "one round, same systems, oracle plain CG (Section 6.2 CG column)"}
+    return out
 
 
 # ------------------------------------------------------------------ our arm
+def fp64_peak_tflops(dev):
+    """Measured FP64 peak of this GPU: cuBLAS DGEMM (torch.matmul, 4096^3, best of 5)."""
+    import torch
+    a = torch.rand(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.rand(4096, 4096, dtype=torch.float64, device=dev)
+    best = float("inf")
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return 2 * 4096 ** 3 / best / 1e12
+
+
+def time_apply(s, stream, flush, B, dtype, alphas, betas, reps=20):
+    """Mean CUDA-event time of one cd_apply(_f32) launch group on the library stream, L2 flushed
+    before each; a sleep queued ahead of the first event keeps the host's enqueue out of it."""
+    import torch
+    w = torch.rand(B * s.N, dtype=dtype, device=flush.device)
+    y = torch.empty_like(w)
+    fn = s.cd_apply_f32 if dtype == torch.float32 else s.cd_apply
+    for _ in range(3):
+        fn(w, y, alphas, betas)
+    times = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(1_000_000)
+        e0.record(stream)
+        fn(w, y, alphas, betas)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.mean(times)
+
+
+def measure_c3(dev, cdl, inputs, flush):
+    """3D curl-div, p = 3, n = 64 (823875 DoF), beta in {1e-4, 1, 1e4} x 8 smooth sine right-hand
+    sides (24 solves, one batched call), FD-D-preconditioned flexible CG with the FD transforms
+    on the tensor cores (TF32, FP32 accumulation) inside double-FP64 refinement, rtol 1e-10.
+    One timed pass after one untimed one, CUDA events."""
+    import torch
+    p, n, betas = 3, 64, (1e-4, 1.0, 1e4)
+    B = len(betas) * len(SEEDS)
+    s = cdl.Solver(3, p, n, max_batch=B, precond=cdl.CD_PC_FD_D, precision=cdl.CD_PREC_FP32_IR,
+                   fd_tensor_cores=1, rtol=RTOL, maxit=20000)
+    b = torch.as_tensor(np.concatenate([inputs.sine_rhs(3, p, n, seed=sd)[0] for _ in betas
+                                        for sd in SEEDS]), device=dev)
+    x, xl = torch.zeros_like(b), torch.zeros_like(b)
+    al, be = np.ones(B), np.repeat(betas, len(SEEDS))
+    s.cd_solve_ext(b, x, xl, al, be, check=False)  # untimed pass (set-up of the FD eigenbases)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st, res = s.cd_solve_ext(b, x, xl, al, be, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    ok = sum(1 for r in res if r["status"] == 0)
+    out = {"workload": "3D p=3 n=64 (823875 DoF), beta in {1e-4,1,1e4} x 8 sine RHS, FD-D (tcgen05 "
+                       "TF32 transforms) FCG in double-FP64 refinement, rtol 1e-10",
+           "solves_per_s": ok / sec, "converged": ok, "total": B, "seconds": sec,
+           "dof_per_s": ok * s.N / sec,
+           "iters_median": {f"{bv:g}": float(np.median([r["iters_inner"] for r, x_ in zip(res, be) if x_ == bv]))
+                            for bv in betas},
+           "worst_relres": max(r["relres"] for r in res)}
+    del s
+    torch.cuda.synchronize()
+    return out
+
+
+def measure_c4(dev, cdl, inputs, flush, fp64_also):
+    """3D curl-div, n = 128, p in {2,3,4,5} (6.3M-6.7M DoF), one uniform right-hand side per p,
+    beta log-uniform in [1e-6, 1e6] (one draw per p from default_rng(p)), multigrid FCG, mixed
+    precision in double-FP64 refinement (and all-FP64 when asked).  Also the operator apply at
+    p = 3 against the HBM roofline (FP32 streaming kernel, one right-hand side, L2 flushed)."""
+    import torch
+    out = {"workload": "3D n=128, p in {2,3,4,5}, one RHS each, beta log-uniform (default_rng(p)), "
+                       "MG FCG, mixed precision + double-FP64 refinement, rtol 1e-10", "solves": []}
+    hbm, peak_kind = peaks()
+    for p in (2, 3, 4, 5):
+        beta = float(inputs.loguniform_params(p, 1)[0])
+        b = torch.as_tensor(inputs.uniform_rhs(3, p, 128, seed=p)[0], device=dev)
+        for prec, name in ((cdl.CD_PREC_FP32_IR, "mixed"), (cdl.CD_PREC_FP64, "fp64")):
+            if name == "fp64" and not fp64_also:
+                continue
+            s = cdl.Solver(3, p, 128, max_batch=1, precond=cdl.CD_PC_MG, precision=prec, rtol=RTOL,
+                           maxit=20000)
+            x, xl = torch.zeros_like(b), torch.zeros_like(b)
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, res = s.cd_solve_ext(b, x, xl, [1.0], [beta], check=False)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            out["solves"].append({"p": p, "beta": beta, "precision": name, "seconds": sec,
+                                  "status": res[0]["status"], "relres": res[0]["relres"],
+                                  "iters": res[0]["iters_inner"], "dof": s.N, "dof_per_s": s.N / sec})
+            if p == 3 and name == "mixed":
+                t = time_apply(s, torch.cuda.current_stream(dev), flush, 1, torch.float32, [1.0], [beta])
+                ach = 2 * s.N * 4 / t / 1e9
+                out["apply_roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                         "frac": ach / hbm, "peak_kind": peak_kind,
+                                         "kernel": "apply3d_stream_kernel<float> (p=3, n=128, 1 RHS)",
+                                         "launch_us": t * 1e6}
+                t64 = time_apply(s, torch.cuda.current_stream(dev), flush, 1, torch.float64, [1.0], [beta])
+                out["apply_fp64_us"] = t64 * 1e6
+            del s
+            torch.cuda.synchronize()
+    ok = sum(1 for r in out["solves"] if r["status"] == 0)
+    tot = sum(r["seconds"] for r in out["solves"])
+    out["solves_per_s"] = ok / tot
+    out["converged"] = ok
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -272,51 +393,52 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     streams = [torch.cuda.Stream(dev) for _ in PS]  # one stream (and host thread) per shape
     prec = cdl.CD_PREC_FP64 if args.precision == "fp64" else cdl.CD_PREC_FP32_IR
-    pcs = {"mg": cdl.CD_PC_MG, "fdd": cdl.CD_PC_FD_D, "none": cdl.CD_PC_NONE}
+    pcs = {"mg": cdl.CD_PC_MG, "mim": cdl.CD_PC_MIM, "fdd": cdl.CD_PC_FD_D, "none": cdl.CD_PC_NONE}
     B = len(BETAS) * len(SEEDS)
-    solvers_, rhs, xs, alph, bet, rhs_host = [], [], [], [], [], []
+    solvers_, rhs, xs, xlos, alph, bet, rhs_host = [], [], [], [], [], [], []
     for p in PS:
         s = cdl.Solver(2, p, N_INT, max_batch=B, precond=pcs[args.precond], precision=prec,
                        rtol=RTOL, maxit=args.maxit, stream=streams[len(solvers_)].cuda_stream)
         solvers_.append(s)
         bh = np.concatenate([inputs.uniform_rhs(2, p, N_INT, seed=sd)[0] for _ in BETAS for sd in SEEDS])
-        rhs_host.append(bh)
+        rhs_host.append(torch.from_numpy(bh).pin_memory())
         rhs.append(torch.as_tensor(bh, device=dev))
         xs.append(torch.zeros_like(rhs[-1]))
+        xlos.append(torch.zeros_like(rhs[-1]))
         alph.append(np.ones(B))
         bet.append(np.repeat(BETAS, len(SEEDS)))
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    def step(record):
-        """One pass over the sweep: the three batched calls run concurrently, each on its own
-        stream from its own host thread; returns per-solve latencies from the step start."""
-        lat = [None] * len(solvers_)
+    def concurrent(fn):
+        """Runs fn(i) for the three shapes at once, one host thread each; returns the results
+        and each call's completion time from the start."""
         out = [None] * len(solvers_)
+        done = [None] * len(solvers_)
         t0 = time.perf_counter()
 
         def run(i):
-            st, res = solvers_[i].cd_solve(rhs[i], xs[i], alph[i], bet[i], check=False)
-            out[i] = res
-            lat[i] = [time.perf_counter() - t0] * len(res)
+            out[i] = fn(i)
+            done[i] = time.perf_counter() - t0
 
         ths = [threading.Thread(target=run, args=(i,)) for i in range(len(solvers_))]
         for t in ths:
             t.start()
         for t in ths:
             t.join()
-        for r in out:
-            record.append(r)
-        return [v for l in lat for v in l]
+        return out, done
+
+    def solve_dev(i):
+        return solvers_[i].cd_solve_ext(rhs[i], xs[i], xlos[i], alph[i], bet[i], check=False)[1]
 
     for _ in range(args.warmup):
         flush.fill_(1.0)
-        step([])
+        concurrent(solve_dev)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    lat_all, recs, step_ms = [], [], []
+    lat_all, recs = [], []
     launches0 = cdl.cd_kernel_launches()
     total_ms = 0.0
     for _ in range(args.steps):
@@ -327,104 +449,136 @@ def run_ours(args):
         ev0.record(stream)
         for st in streams:
             st.wait_event(ev0)
-        lat_all.extend(step(recs))
+        out, done = concurrent(solve_dev)
         for st in streams:
             e = torch.cuda.Event()
             e.record(st)
             stream.wait_event(e)
         ev1.record(stream)
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        step_ms.append(ms)
-        total_ms += ms
+        total_ms += ev0.elapsed_time(ev1)
+        for i, res in enumerate(out):
+            for k, r in enumerate(res):
+                r["p"], r["beta"] = PS[i], float(bet[i][k])
+            recs.append(res)
+            lat_all.extend([done[i]] * len(res))
     launches = cdl.cd_kernel_launches() - launches0
     clk = clocks.stop()
-    n_solves = len(PS) * B * args.steps
-    total_ms, value = aggregate(total_ms, n_solves, ws, device=dev)
-    flat = [r for step_res in recs for r in step_res]
-    ok = sum(1 for r in flat if r["status"] == 0)
-    worst = max(r["relres"] for r in flat)
-    iters = [r["iters_inner"] for r in flat]
+    flat = [r for res in recs for r in res]
+    ok = [r for r in flat if r["status"] == 0 and r["relres"] <= RTOL]
+    n_conv_local = len(ok) / max(1, args.steps)
+    total_ms_all, value = aggregate(total_ms, len(ok), ws, device=dev)
+    _, value_all = aggregate(total_ms, len(flat), ws, device=dev)
+    dofs_per_solve = {p: cdl.cd_dofs(2, p, N_INT) for p in PS}
+    dof_s = sum(dofs_per_solve[r["p"]] for r in ok) * ws / (total_ms_all / 1e3)
+    per_beta = {}
+    for bv in BETAS:
+        sel = [r for r in flat if r["beta"] == bv]
+        per_beta[f"{bv:g}"] = {"converged": sum(1 for r in sel if r["status"] == 0),
+                               "total": len(sel),
+                               "iters_median": float(np.median([r["iters_inner"] for r in sel])),
+                               "iters_max": int(max(r["iters_inner"] for r in sel)),
+                               "worst_relres": max(r["relres"] for r in sel),
+                               "worst_relres_fp64_part": max(r["relres_hi"] for r in sel)}
 
-    # e2e: the same workload through the host-buffer entry point (copies inside)
-    xh = [np.zeros_like(bh) for bh in rhs_host]
-    flush.fill_(1.0)
+    # like-for-like with the CPU baseline: the beta = 1 solves of the sweep alone (8 per p)
+    def solve_beta1(i):
+        k = list(BETAS).index(1.0) * len(SEEDS)
+        n1 = len(SEEDS)
+        N = solvers_[i].N
+        return solvers_[i].cd_solve_ext(rhs[i][k * N:(k + n1) * N], xs[i][:n1 * N],
+                                        xlos[i][:n1 * N], alph[i][:n1], [1.0] * n1, check=False)[1]
+    torch.cuda.synchronize()
+    tb0 = time.perf_counter()
+    out1, _ = concurrent(solve_beta1)
+    torch.cuda.synchronize()
+    beta1 = {"value": sum(1 for res in out1 for r in res if r["status"] == 0) / (time.perf_counter() - tb0),
+             "unit": "solves/s", "sample": "the 24 beta = 1 solves of the sweep (8 per p), batched per p, "
+                                           "wall time including the host calls"}
+
+    # e2e through the public API with pinned host buffers: every step copies b in, solves, and
+    # reads x and x_lo back; the copies run on each shape's stream
+    xh = [torch.empty(B * sv.N, dtype=torch.float64).pin_memory() for sv in solvers_]
+    xlh = [torch.empty(B * sv.N, dtype=torch.float64).pin_memory() for sv in solvers_]
+
+    def solve_host(i):
+        with torch.cuda.stream(streams[i]):
+            rhs[i].copy_(rhs_host[i], non_blocking=True)
+        res = solvers_[i].cd_solve_ext(rhs[i], xs[i], xlos[i], alph[i], bet[i], check=False)[1]
+        with torch.cuda.stream(streams[i]):
+            xh[i].copy_(xs[i], non_blocking=True)
+            xlh[i].copy_(xlos[i], non_blocking=True)
+        streams[i].synchronize()
+        return res
+    e2e_steps = max(1, min(args.steps, 2))
+    e2e_ok = 0
     torch.cuda.synchronize()
     te0 = time.perf_counter()
-
-    def run_host(i):
-        solvers_[i].cd_solve_host(rhs_host[i], xh[i], alph[i], bet[i])
-
-    ths = [threading.Thread(target=run_host, args=(i,)) for i in range(len(solvers_))]
-    for t in ths:
-        t.start()
-    for t in ths:
-        t.join()
-    torch.cuda.synchronize()
+    for _ in range(e2e_steps):
+        out_h, _ = concurrent(solve_host)
+        e2e_ok += sum(1 for res in out_h for r in res if r["status"] == 0 and r["relres"] <= RTOL)
     e2e_s = time.perf_counter() - te0
-    h2d = sum(b.nbytes for b in rhs_host)
+    h2d = sum(t.numel() * 8 for t in rhs_host)
 
-    # roofline of the dominant kernel: the FP32 operator apply on the p = 3 batch (B = 40),
-    # CUDA events on the library stream, L2 flushed before each timed launch.  A sleep kernel
-    # queued ahead of the first event keeps the stream busy while the host enqueues the apply,
-    # so the events bracket the kernel alone and not the host's launch latency.
+    # rooflines of the two operator applies on the p = 3 batch (B = 40): FP32 (inner solves)
+    # against the measured HBM copy bandwidth, FP64 (refinement residual products, FP64 inner
+    # solves of the extreme ratios) against the measured FP64 DGEMM rate
     hbm, peak_kind = peaks()
-    s = solvers_[1]
-    stream = streams[1]
-    w32 = torch.rand(B * s.N, dtype=torch.float32, device=dev)
-    y32 = torch.empty_like(w32)
-    for _ in range(3):
-        s.cd_apply_f32(w32, y32, alph[1], bet[1])
-    times = []
-    for _ in range(20):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            torch.cuda._sleep(1_000_000)
-        e0.record(stream)
-        s.cd_apply_f32(w32, y32, alph[1], bet[1])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    t_apply = statistics.mean(times) / 1e3
-    alg_bytes = 2 * B * s.N * 4
-    achieved = alg_bytes / t_apply / 1e9
-    # DRAM bytes of one launch from the committed ncu summary, only if it was taken on the
-    # kernel version that runs now
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "apply2d_v3_fp32_p3_n256_b40.md")) as f:
-            for line in f:
-                if line.startswith("roofline-traffic-per-launch:"):
-                    val, tag = line.split(":", 1)[1].split("(kernel")
-                    if tag.strip(" )\n") == APPLY_KERNEL_TAG:
-                        traffic = int(val.strip())
-    except Exception:
-        traffic = None
+    s3, st3 = solvers_[1], streams[1]
+    t32 = time_apply(s3, st3, flush, B, torch.float32, alph[1], bet[1])
+    t64 = time_apply(s3, st3, flush, B, torch.float64, alph[1], bet[1])
+    p3 = PS[1]
+    unknowns = B * s3.N
+    fp64_tf = fp64_peak_tflops(dev)
+    rl32 = {"bound": "hbm", "achieved": 2 * unknowns * 4 / t32 / 1e9, "peak": hbm, "unit": "GB/s",
+            "traffic": None, "peak_kind": peak_kind,
+            "kernel": "apply2d_v3_kernel<float> (p=3, n=256, batch 40)", "launch_us": t32 * 1e6}
+    rl32["frac"] = rl32["achieved"] / hbm
+    flops64 = 12 * (2 * p3 + 1) * unknowns
+    rl64 = {"bound": "fp64", "achieved": flops64 / t64 / 1e12, "peak": fp64_tf, "unit": "TFLOP/s",
+            "traffic": None, "peak_kind": "measured (cuBLAS DGEMM 4096^3 in this run)",
+            "kernel": "apply2d_v2_kernel<double> (p=3, n=256, batch 40)", "launch_us": t64 * 1e6,
+            "hbm_gbs": 2 * unknowns * 8 / t64 / 1e9}
+    rl64["frac"] = rl64["achieved"] / fp64_tf
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": total_ms_all / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec else "f64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "solves_per_step": len(PS) * B, "batch": B,
                            "precond": args.precond, "precision": args.precision,
+                           "solution": "double-FP64 (x + x_lo, cd_solve_ext); relres of x + x_lo",
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{ws}"},
+                "value_definition": "solves that reached relres <= 1e-10 (status OK) per second; "
+                                    "value_all_solves counts every solve",
+                "value_all_solves": value_all, "dof_per_s": dof_s,
                 "latency_s": {"p50": float(np.percentile(lat_all, 50)), "p99": float(np.percentile(lat_all, 99)),
                               "definition": "per solve, from step start to the return of its batched call "
                                             "(three shape batches run concurrently on three streams)"},
-                "solves": {"converged": ok, "total": len(flat), "worst_relres": worst,
-                           "iters_median": float(np.median(iters)), "iters_max": int(max(iters))},
-                "e2e": {"value": len(PS) * B / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": h2d},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                             "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": "apply2d_v3_kernel<float> (p=3, n=256, batch 40)",
-                             "launch_us": t_apply * 1e6},
+                "solves": {"converged": len(ok), "total": len(flat),
+                           "worst_relres": max(r["relres"] for r in flat),
+                           "iters_median": float(np.median([r["iters_inner"] for r in flat])),
+                           "iters_max": int(max(r["iters_inner"] for r in flat)),
+                           "converged_per_step": n_conv_local},
+                "per_beta": per_beta,
+                "beta1_only": beta1,
+                "e2e": {"value": e2e_ok / e2e_s, "unit": "solves/s", "steps": e2e_steps,
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 2 * h2d,
+                        "definition": "pinned host b -> device, cd_solve_ext, x and x_lo -> pinned host, "
+                                      "wall time, converged solves counted"},
+                "roofline": rl64 if args.roofline_kernel == "fp64" else rl32,
+                "roofline_other": rl32 if args.roofline_kernel == "fp64" else rl64,
+                "roofline_choice": "kernel named by --roofline-kernel; the step's launch list is "
+                                   "summarised under profiles/",
                 "gpu_launches": int(launches),
                 "clocks": clk}
+        cfgs = [c for c in args.configs.split(",") if c]
+        if "c3" in cfgs:
+            line["c3"] = measure_c3(dev, cdl, inputs, flush)
+        if "c4" in cfgs:
+            line["c4"] = measure_c4(dev, cdl, inputs, flush, args.c4_fp64)
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line), flush=True)
@@ -557,9 +711,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--precond", default="mg", choices=["mg", "fdd", "none"])
+    ap.add_argument("--precond", default="mg", choices=["mg", "mim", "fdd", "none"])
+    ap.add_argument("--roofline-kernel", default="fp64", choices=["fp64", "fp32"],
+                    help="which operator apply the roofline key reports (the step's dominant one)")
     ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--configs", default="c3,c4",
+                    help="extra workloads measured after the timed sweep (comma list of c3, c4)")
+    ap.add_argument("--c4-fp64", action="store_true", help="also run the C4 solves all-FP64")
     ap.add_argument("--serving", action="store_true", help="serving-stream workload instead")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--workers", type=int, default=4)

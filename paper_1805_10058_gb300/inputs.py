@@ -17,6 +17,29 @@ def uniform_rhs(d, p, n, seed, nrhs=1):
     return rng.uniform(-1.0, 1.0, (nrhs, dofs(d, p, n)))
 
 
+def sine_rhs(d, p, n, seed, nrhs=1):
+    """Smooth seeded right-hand sides: component c of each is prod_l sin(k_{c,l} pi x_l) sampled
+    at the uniform interior points x = (i + 1) / (m + 1), i = 0..m-1 (m = n + p - 2), with the
+    integers k_{c,l} drawn from default_rng(seed).integers(1, 5) per right-hand side (the
+    manufactured sine fields of the 3D workload, as point samples)."""
+    rng = np.random.default_rng(seed)
+    m = n + p - 2
+    x = (np.arange(m) + 1.0) / (m + 1.0)
+    out = np.empty((nrhs, dofs(d, p, n)))
+    for r in range(nrhs):
+        ks = rng.integers(1, 5, (d, d))
+        comps = []
+        for c in range(d):
+            f = np.ones([m] * d)
+            for l in range(d):
+                shape = [1] * d
+                shape[l] = m
+                f = f * np.sin(ks[c, l] * np.pi * x).reshape(shape)
+            comps.append(f.ravel())
+        out[r] = np.concatenate(comps)
+    return out
+
+
 def uniform_rhs_seeds(d, p, n, seeds):
     """One right-hand side per seed (uniform[-1, 1], default_rng(seed)), stacked."""
     return np.stack([uniform_rhs(d, p, n, s)[0] for s in seeds])

@@ -70,9 +70,9 @@ def test_lanczos_extremes_match_dense_eigenvalues(d, p, n, beta):
 def test_lanczos_extremes_obey_the_laplacian_bounds_at_benchmark_size():
     """n = 256, p = 3: the matrix form of Theorem 5.2 puts the spectrum of A between
     min(alpha,beta) and max(alpha,beta) times that of the block Laplacian K = A(1, 1); the
-    Lanczos estimates of the largest eigenvalues obey it, and the largest eigenvalue of A (scaled
-    as in Section 5.3, n^{d-2} = 1 in 2D) is close to the maximum of the symbol samples (the
-    spectral distribution of Theorem 5.1, up to the few outliers of the boundary rows)."""
+    Lanczos estimates of the largest eigenvalues obey it.  (The largest eigenvalue of A itself lies
+    above the maximum of the symbol samples: measured 1.57 against 1.09 at beta = 1e-3, an outlier
+    of the boundary rows, which the spectral distribution of Theorem 5.1 does not constrain.)"""
     d, p, n = 2, 3, 256
     s = cdl.Solver(d, p, n, max_batch=3)
     v0 = torch.as_tensor(inputs.uniform_rhs(d, p, n, seed=4, nrhs=3).ravel(), device="cuda")
@@ -83,5 +83,5 @@ def test_lanczos_extremes_obey_the_laplacian_bounds_at_benchmark_size():
         hi = max(1.0, betas[k])
         assert lmax[k] <= hi * kmax * (1 + 1e-6), (lmax[k], kmax)
         assert lmin[k] > 0
-        lam, _ = gpu_symbol(d, p, 1.0, betas[k], 256)
-        assert abs(lmax[k] - lam.max()) <= 0.1 * lam.max(), (lmax[k], lam.max())
+        lo = min(1.0, betas[k])
+        assert lmax[k] >= lo * kmax * (1 - 1e-6), (lmax[k], kmax)
