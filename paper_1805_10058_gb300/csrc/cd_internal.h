@@ -101,7 +101,12 @@ void unregister_level(const void* bands_dev);
 void set_apply_variant(int v);
 // 3D apply: 1 = streaming fused kernel (default), 0 = three banded passes (kept for checks).
 void set_apply3d_variant(int v);
-void set_apply_fp64_variant(int v);  // 2D FP64: 0 = v2, 1 = v3
+void set_apply_fp64_variant(int v);  // 2D FP64: 0 = v2, 1 = v3, 2 = double-FP32 everywhere
+// The calling thread's FP64 2D applies (modes 0 and 1) run in double-FP32 arithmetic on the
+// FP32 pipe while set (the inner FP64 Krylov solves of the refinement loop); fp64_emulated()
+// tells whether they do now.
+void set_fp64_emulated(int on);
+int fp64_emulated();
 
 // Autotuner of the 2D apply: times the variants on (m, P, B) and records the fastest
 // (returns the chosen variant, 0 if none was tuned).  Not inside a stream capture.

@@ -1157,9 +1157,231 @@ static int tuned_variant(size_t es, int m, int P, int /*B*/) {
 }
 static int g_use_v2 = 2;  // 2: v3 kernel, 1: v2 kernel, 0: v1 kernel
 void set_apply_variant(int v) { g_use_v2 = v; }
-static int g_fp64_v3 = 0;  // FP64 2D apply: 0 = v2 (default), 1 = v3 (8 rows per tile)
-void set_apply_fp64_variant(int v) { g_fp64_v3 = v; }
+static int g_fp64_v3 = 0;    // FP64 2D apply: 0 = v2 (default), 1 = v3 (8 rows per tile)
+static int g_ff_forced = 0;  // 2: every FP64 2D apply in double-FP32 (kernel checks)
+void set_apply_fp64_variant(int v) {
+  g_fp64_v3 = v == 1;
+  g_ff_forced = v == 2;
+}
 void set_apply3d_variant(int v) { g_use_stream3d = v; }
+
+// ------------------------------------------------------------------ 2D apply in double-FP32
+// FP64 vectors, arithmetic in double-FP32 ("float-float": an unevaluated sum hi + lo of two FP32
+// numbers, about 48 significant bits) on the FP32 pipe, which on GB300 issues 64 times the FP64
+// rate.  Each FP64 input element of the tile is split once into (hi, lo) in shared memory; every
+// product is an FMA two-product with the cross terms, every sum a two-sum (non-contracting _rn
+// intrinsics); the x_2 results, scaled and grouped as in the FP32 kernel (PM, PS, PA), stay in
+// shared memory as (hi, lo) pairs, and the x_1 pass forms y in double-FP32 and rounds it to FP64.
+// Accuracy: about 1e-13 of (|A| |w|)_i, 30x coarser than FP64, used for the inner Krylov solves
+// of the refinement loop (whose double-FP64 outer residual removes it).
+struct StencilFF {
+  float2 c[3][13];
+  int lo, hi;
+};
+
+__device__ __forceinline__ float2 ff_split(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(__dsub_rn(v, (double)h)));
+}
+// acc += c * x (all double-FP32)
+__device__ __forceinline__ void ff_fma(float2& acc, float2 c, float2 x) {
+  const float p = __fmul_rn(c.x, x.x);
+  float e = __fmaf_rn(c.x, x.x, -p);
+  e = __fmaf_rn(c.x, x.y, e);
+  e = __fmaf_rn(c.y, x.x, e);
+  const float sm = __fadd_rn(acc.x, p);
+  const float bb = __fsub_rn(sm, acc.x);
+  const float er = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(sm, bb)), __fsub_rn(p, bb));
+  acc.y = __fadd_rn(acc.y, __fadd_rn(er, e));
+  acc.x = sm;
+}
+__device__ __forceinline__ float2 ff_norm(float2 a) {
+  const float sm = __fadd_rn(a.x, a.y);
+  return make_float2(sm, __fsub_rn(a.y, __fsub_rn(sm, a.x)));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  float2 acc = make_float2(0.f, 0.f);
+  ff_fma(acc, a, b);
+  return ff_norm(acc);
+}
+__device__ __forceinline__ double ff_to_double(float2 a) {
+  return __dadd_rn((double)a.x, (double)a.y);
+}
+
+template <int P, int TR>
+__global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
+    int m, const double* __restrict__ bandT, StencilFF cs, const double* __restrict__ w,
+    double* __restrict__ y, const double* __restrict__ rhs, int mode,
+    const double* __restrict__ alpha, const double* __restrict__ beta,
+    const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp) {
+  constexpr int W = 2 * P + 1, TC = 64, HR = TR + 2 * P, HC = TC + 2 * P;
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sw = reinterpret_cast<float2*>(smem_raw);  // [2][HR][HC] input tile, (hi, lo)
+  float2* sp = sw + 2 * HR * HC;                      // [3][2][HR][TC] intermediates
+  const long long N = 2LL * m * m;
+  const double* wb = w + (long long)b * N;
+  const int c0 = blockIdx.x * TC, r0 = blockIdx.y * TR;
+  const float2 al = ff_split(alpha[b]), be = ff_split(beta[b]);
+  const float2 ga = ff_split((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
+  const double* BM = bandT;
+  const double* BA = bandT + (size_t)W * m;
+  const double* BS = bandT + (size_t)2 * W * m;
+  // tile of w with halos, split once
+  for (int idx = threadIdx.x; idx < 2 * HR * HC; idx += blockDim.x) {
+    const int c = idx / (HR * HC), rem = idx - c * HR * HC;
+    const int rr = rem / HC, cc = rem - rr * HC;
+    const int row = r0 - P + rr, col = c0 - P + cc;
+    float2 v = make_float2(0.f, 0.f);
+    if (row >= 0 && row < m && col >= 0 && col < m) v = ff_split(wb[(long long)c * m * m + (long long)row * m + col]);
+    sw[idx] = v;
+  }
+  __syncthreads();
+  // axis x_2 for rows r0-P .. r0+TR+P-1: S2, M2, A2 of both components, scaled and grouped
+  for (int item = threadIdx.x; item < HR * TC; item += blockDim.x) {
+    const int q = item / TC, cc = item - q * TC;
+    const int row = r0 - P + q, j = c0 + cc;
+    float2 tM[2], tA[2], tS[2];
+    for (int c = 0; c < 2; ++c) tM[c] = tA[c] = tS[c] = make_float2(0.f, 0.f);
+    if (row >= 0 && row < m && j < m) {
+      const bool interior = j >= cs.lo && j < cs.hi;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        float2 cM, cA, cS;
+        if (interior) {
+          cM = cs.c[0][k];
+          cA = cs.c[1][k];
+          cS = cs.c[2][k];
+        } else {
+          cM = ff_split(BM[(size_t)k * m + j]);
+          cA = ff_split(BA[(size_t)k * m + j]);
+          cS = ff_split(BS[(size_t)k * m + j]);
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float2 v = sw[(c * HR + q) * HC + cc + k];
+          ff_fma(tM[c], cM, v);
+          ff_fma(tA[c], cA, v);
+          ff_fma(tS[c], cS, v);
+        }
+      }
+      for (int c = 0; c < 2; ++c) {
+        tM[c] = ff_norm(tM[c]);
+        tA[c] = ff_norm(tA[c]);
+        tS[c] = ff_norm(tS[c]);
+      }
+    }
+    // PM = (alpha S2 w1, beta S2 w2) feeds M1; PS = (beta M2 w1, alpha M2 w2) feeds S1;
+    // PA = gamma (A2 w2, A2 w1) feeds A1
+    sp[((0 * 2 + 0) * HR + q) * TC + cc] = ff_mul(al, tS[0]);
+    sp[((0 * 2 + 1) * HR + q) * TC + cc] = ff_mul(be, tS[1]);
+    sp[((1 * 2 + 0) * HR + q) * TC + cc] = ff_mul(be, tM[0]);
+    sp[((1 * 2 + 1) * HR + q) * TC + cc] = ff_mul(al, tM[1]);
+    sp[((2 * 2 + 0) * HR + q) * TC + cc] = ff_mul(ga, tA[1]);
+    sp[((2 * 2 + 1) * HR + q) * TC + cc] = ff_mul(ga, tA[0]);
+  }
+  __syncthreads();
+  // axis x_1: y_c = M1 PM_c + S1 PS_c + A1 PA_c
+  double acc = 0.0;
+  for (int item = threadIdx.x; item < TR * TC; item += blockDim.x) {
+    const int r = item / TC, cc = item - r * TC;
+    const int i = r0 + r, j = c0 + cc;
+    if (i >= m || j >= m) continue;
+    const bool interior = i >= cs.lo && i < cs.hi;
+    float2 yy[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      float2 cM, cA, cS;
+      if (interior) {
+        cM = cs.c[0][k];
+        cA = cs.c[1][k];
+        cS = cs.c[2][k];
+      } else {
+        cM = ff_split(BM[(size_t)k * m + i]);
+        cA = ff_split(BA[(size_t)k * m + i]);
+        cS = ff_split(BS[(size_t)k * m + i]);
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        ff_fma(yy[c], cM, sp[((0 * 2 + c) * HR + r + k) * TC + cc]);
+        ff_fma(yy[c], cS, sp[((1 * 2 + c) * HR + r + k) * TC + cc]);
+        ff_fma(yy[c], cA, sp[((2 * 2 + c) * HR + r + k) * TC + cc]);
+      }
+    }
+    const long long o1 = (long long)b * N + (long long)i * m + j, o2 = o1 + (long long)m * m;
+    double y1 = ff_to_double(ff_norm(yy[0])), y2 = ff_to_double(ff_norm(yy[1]));
+    if (mode == 1) {
+      y1 = rhs[o1] - y1;
+      y2 = rhs[o2] - y2;
+      if (dotp) acc += y1 * y1 + y2 * y2;
+    } else if (dotp) {
+      acc += w[o1] * y1 + w[o2] * y2;
+    }
+    y[o1] = y1;
+    y[o2] = y2;
+  }
+  if (dotp) {
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0)
+      dotp[(size_t)b * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+template <int P, int TR>
+static size_t ff_smem() {
+  return sizeof(float2) * ((size_t)2 * (TR + 2 * P) * (64 + 2 * P) + (size_t)6 * (TR + 2 * P) * 64);
+}
+template <int P, int TR>
+static void set_ff_attr() {
+  cudaFuncSetAttribute(apply2d_ff_kernel<P, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ff_smem<P, TR>());
+}
+
+template <int P>
+static bool launch_ff_P(int m, const double* bands, const StencilHost& sh, const double* w, double* y,
+                        const double* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                        const int* active, cudaStream_t s) {
+  constexpr int TR = 16;
+  StencilFF cs;
+  for (int x = 0; x < 3; ++x)
+    for (int k = 0; k < 13; ++k) {
+      const double v = k < 2 * P + 1 ? sh.c[x][k] : 0.0;
+      const float h = (float)v;
+      cs.c[x][k] = make_float2(h, (float)(v - (double)h));
+    }
+  cs.lo = sh.lo;
+  cs.hi = sh.hi;
+  dim3 grid((m + 63) / 64, (m + TR - 1) / TR, B);
+  apply2d_ff_kernel<P, TR><<<grid, 256, ff_smem<P, TR>(), s>>>(
+      m, bands + (size_t)3 * m * (2 * P + 1), cs, w, y, rhs, mode, c.alpha, c.beta, c.gsc, active,
+      dotp);
+  count_launch();
+  if (nblk) *nblk = grid.x * grid.y;
+  return true;
+}
+
+static thread_local int g_ff_inner = 0;  // the calling thread's FP64 applies run in double-FP32
+void set_fp64_emulated(int on) { g_ff_inner = on; }
+int fp64_emulated() { return g_ff_inner || g_ff_forced; }
+
+static bool try_apply2d_ff(int m, int P, const double* bands, const double* w, double* y,
+                           const double* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                           const int* active, cudaStream_t s) {
+  if (mode == 2) return false;
+  StencilHost sh;
+  if (!find_level(bands, sh) || sh.P != P) return false;
+  if (dotp && (long long)((m + 63) / 64) * ((m + 15) / 16) > kMaxPartials) return false;
+  switch (P) {
+    case 1: return launch_ff_P<1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 2: return launch_ff_P<2>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 3: return launch_ff_P<3>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 4: return launch_ff_P<4>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 5: return launch_ff_P<5>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 6: return launch_ff_P<6>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    default: return false;
+  }
+}
 
 int prepare_kernels() {
   set_stream3d_attr<float, 1>(); set_stream3d_attr<float, 2>(); set_stream3d_attr<float, 3>();
@@ -1172,6 +1394,8 @@ int prepare_kernels() {
   set_v2_attrs<float, 4>(); set_v2_attrs<float, 5>(); set_v2_attrs<float, 6>();
   set_v2_attrs<double, 1>(); set_v2_attrs<double, 2>(); set_v2_attrs<double, 3>();
   set_v2_attrs<double, 4>(); set_v2_attrs<double, 5>(); set_v2_attrs<double, 6>();
+  set_ff_attr<1, 16>(); set_ff_attr<2, 16>(); set_ff_attr<3, 16>();
+  set_ff_attr<4, 16>(); set_ff_attr<5, 16>(); set_ff_attr<6, 16>();
   cudaError_t e1 = cudaFuncSetAttribute(apply2d_kernel<double>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmemCap);
   cudaError_t e2 = cudaFuncSetAttribute(apply2d_kernel<float>,
@@ -1207,6 +1431,11 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
     g_epi<T> = Epi<T>{};
   }
   if (d == 2) {
+    if constexpr (sizeof(T) == 8) {
+      if (mode != 2 && fp64_emulated() &&
+          try_apply2d_ff(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+        return 0;
+    }
     if (sizeof(T) == 8 && g_use_v2 == 2 && g_fp64_v3 &&
         try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, 8))
       return 0;
@@ -1362,6 +1591,7 @@ template int tune_apply2d<double>(int, int, const double*, const double*, double
 template <typename T>
 bool apply_can_fuse(int d, int m, int P, const T* bands, int B) {
   if (d == 3) return true;
+  if (sizeof(T) == 8 && fp64_emulated()) return false;  // the double-FP32 apply has no mode 2
   if (g_use_v2 < 1 || P < 1 || P > 6) return false;
   StencilHost sh;
   if (!find_level(bands, sh)) return false;

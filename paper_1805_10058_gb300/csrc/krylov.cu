@@ -229,7 +229,7 @@ __global__ void ir_check_kernel(int B, const double* part_rr, int nrr, const dou
                                 double* rnorm, double* rrprev, int* active, int* status,
                                 double* relres, int* outer_it, int* grp, double* tol2v,
                                 double tol2, double inner2, int max_outer,
-                                const int* inner_total, int maxit) {
+                                const int* inner_total, int maxit, double floor2) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B || !active[b]) return;
   const double rr = psum(part_rr, nrr, b);
@@ -265,7 +265,7 @@ __global__ void ir_check_kernel(int B, const double* part_rr, int nrr, const dou
   } else {
     // aim at the final tolerance: rtol ||b|| relative to the current residual
     double t = tol2 * bnorm2[b] / rr;
-    tol2v[b] = fmin(fmax(t, 1e-30), 0.25);
+    tol2v[b] = fmin(fmax(t, floor2), 0.25);
   }
 }
 
@@ -533,10 +533,10 @@ void count_active(int B, const int* active, int* out, cudaStream_t s) {
 void ir_check(int B, const double* prr, int nrr, const double* bnorm2, double* rnorm,
               double* rrprev, int* active, int* status, double* relres, int* outer_it, int* grp,
               double* tol2v, double tol2, double inner2, int max_outer, const int* inner_total,
-              int maxit, cudaStream_t s) {
+              int maxit, double floor2, cudaStream_t s) {
   ir_check_kernel<<<sgrid(B), 128, 0, s>>>(B, prr, nrr, bnorm2, rnorm, rrprev, active, status,
                                            relres, outer_it, grp, tol2v, tol2, inner2, max_outer,
-                                           inner_total, maxit);
+                                           inner_total, maxit, floor2);
   count_launch();
 }
 void group_masks(int B, const int* active, const int* grp, int* m0, int* m1, int* m2, int* out,

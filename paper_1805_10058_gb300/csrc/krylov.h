@@ -74,7 +74,7 @@ void count_active(int B, const int* active, int* out, cudaStream_t s);
 void ir_check(int B, const double* prr, int nrr, const double* bnorm2, double* rnorm,
               double* rrprev, int* active, int* status, double* relres, int* outer_it, int* grp,
               double* tol2v, double tol2, double inner2, int max_outer, const int* inner_total,
-              int maxit, cudaStream_t s);
+              int maxit, double floor2, cudaStream_t s);
 void group_masks(int B, const int* active, const int* grp, int* m0, int* m1, int* m2, int* out,
                  cudaStream_t s);
 void scale_div(long long N, int B, const double* src, double* dst, const double* rnorm,

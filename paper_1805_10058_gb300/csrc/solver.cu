@@ -283,7 +283,7 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
   cudaGraphExec_t exec = nullptr;
   uint64_t nodes = 0;
   if (h->opt.use_graphs) {
-    auto key = std::make_tuple((int)(sizeof(T) == 4), B, pc, flexible, 0, maxit);
+    auto key = std::make_tuple((int)(sizeof(T) == 4), B, pc, flexible, fp64_emulated(), maxit);
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
       exec = it->second.first;
@@ -478,7 +478,7 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, double* x
              h->ir_rrprev.as<double>(), act, h->ir_status.as<int>(), h->ir_relres.as<double>(),
              h->ir_outer.as<int>(), h->ir_grp.as<int>(), h->ir_tol2.as<double>(),
              h->opt.rtol * h->opt.rtol, inner2, h->opt.max_outer, h->ir_inner_total.as<int>(),
-             h->opt.maxit, h->s);
+             h->opt.maxit, (ext && h->opt.emulated_fp64 && h->d == 2) ? 1e-12 : 1e-30, h->s);
     group_masks(B, act, h->ir_grp.as<int>(), m[0], m[1], m[2], h->cnt.as<int>(), h->s);
     CD_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->cnt.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
     CD_CUDA_OK(cudaStreamSynchronize(h->s));
@@ -506,7 +506,12 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, double* x
       // keeps the whole budget (the outer check stops a solve at maxit iterations in total).
       const int cap = (step == 0 || ext) ? h->opt.maxit
                                          : std::min({h->opt.maxit, h->opt.inner_maxit, 500});
+      // 2D: the inner FP64 solve applies the operator in double-FP32 on the FP32 pipe (the
+      // double-FP64 outer residual corrects its coarser rounding)
+      const bool emu = ext && h->opt.emulated_fp64 && h->d == 2;
+      set_fp64_emulated(emu ? 1 : 0);
       cd_status st = run_pcg<double>(h, B, pc, tol2v, cap, m[g]);
+      set_fp64_emulated(0);
       if (st != CD_OK) return st;
       add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), m[g],
                                                           h->ir_inner_total.as<int>());
@@ -664,6 +669,7 @@ void cd_default_options(cd_options* o) {
   o->fd_tensor_cores = 1;
   o->autotune = 1;
   o->ext_residual = 1;
+  o->emulated_fp64 = 1;
 }
 
 size_t cd_dofs(int d, int p, int n) {
@@ -836,7 +842,8 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     const std::string vs = v ? v : "";
     set_apply_variant(vs == "v1" ? 0 : vs == "v2" ? 1 : 2);
     const char* v64 = std::getenv("CURLDIV_APPLY_KERNEL_FP64");
-    set_apply_fp64_variant(v64 && std::string(v64) == "v3" ? 1 : 0);
+    const std::string v64s = v64 ? v64 : "";
+    set_apply_fp64_variant(v64s == "v3" ? 1 : v64s == "ff" ? 2 : 0);
     const char* v3d = std::getenv("CURLDIV_APPLY3D_KERNEL");
     set_apply3d_variant(v3d && std::string(v3d) == "multipass" ? 0 : 1);
   }

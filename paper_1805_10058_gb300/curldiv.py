@@ -25,7 +25,7 @@ class Options(ctypes.Structure):
                 ("mg_m_min", ctypes.c_int), ("use_graphs", ctypes.c_int), ("chunk", ctypes.c_int),
                 ("mixed_switch_ratio", ctypes.c_double), ("fd_tensor_cores", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("ext_residual", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("emulated_fp64", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class Result(ctypes.Structure):

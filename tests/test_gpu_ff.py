@@ -1,0 +1,60 @@
+"""The 2D operator apply in double-FP32 arithmetic (FP64 vectors, float-float products and sums
+on the FP32 pipe) through the C-ABI: elementwise against the oracle's assembled matrix, and the
+refinement loop's inner FP64 solves with it (emulated_fp64) against the same solves with FP64
+applies."""
+import numpy as np
+import pytest
+
+from gpu_helpers import abs_matvec_bound, oracle_matrix
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1805_10058_gb300 import curldiv as cdl  # noqa: E402
+from paper_1805_10058_gb300 import inputs  # noqa: E402
+
+# about 48 significant bits per operation over <= 3 (2p+1) terms per pass and two passes
+FF_TOL = 5e-13
+
+
+@pytest.mark.parametrize("p,n,beta", [(1, 9, 1.0), (2, 40, 1e-6), (3, 70, 1e3), (4, 33, 0.01),
+                                      (6, 30, 1e6), (3, 256, 1e-3)])
+def test_double_fp32_apply_matches_oracle(p, n, beta, monkeypatch):
+    monkeypatch.setenv("CURLDIV_APPLY_KERNEL_FP64", "ff")
+    d, B = 2, 3
+    W = inputs.uniform_rhs(d, p, n, seed=31, nrhs=B)
+    s = cdl.Solver(d, p, n, 1.0, beta, max_batch=B, autotune=0)
+    w = torch.as_tensor(W.ravel(), device="cuda")
+    y = torch.zeros_like(w)
+    s.cd_apply(w, y)
+    Y = y.cpu().numpy().reshape(B, -1)
+    A = oracle_matrix(d, p, n, 1.0, beta)
+    worst = 0.0
+    for k in range(B):
+        bound = abs_matvec_bound(A, W[k])
+        err = np.abs(Y[k] - A @ W[k]) / bound
+        worst = max(worst, float(err.max()))
+    print("double-FP32 apply, worst error / (|A||w|):", p, n, beta, worst)
+    assert worst <= FF_TOL, worst
+
+
+@pytest.mark.parametrize("p,n", [(2, 62), (3, 61)])
+def test_emulated_inner_solves_reach_rtol_like_fp64(p, n):
+    """Extreme and moderate ratios in one batch: with double-FP32 inner applies the refinement loop
+    still reaches rtol = 1e-10 for x + x_lo, in a comparable number of inner iterations."""
+    betas = [1e-6, 1e-3, 1.0, 1e6]
+    B = len(betas)
+    Bv = inputs.uniform_rhs(2, p, n, seed=2, nrhs=B)
+    b = torch.as_tensor(Bv.ravel(), device="cuda")
+    out = {}
+    for emu in (1, 0):
+        s = cdl.Solver(2, p, n, max_batch=B, precond=cdl.CD_PC_MG, rtol=1e-10, maxit=40000,
+                       emulated_fp64=emu)
+        x, xl = torch.zeros_like(b), torch.zeros_like(b)
+        st, res = s.cd_solve_ext(b, x, xl, [1.0] * B, betas, check=False)
+        assert st == cdl.CD_OK, (emu, res)
+        assert all(r["relres"] <= 1e-10 for r in res), (emu, res)
+        out[emu] = [r["iters_inner"] for r in res]
+    print("inner iterations emulated / FP64:", out[1], out[0])
+    for k in range(B):
+        assert out[1][k] <= 1.6 * out[0][k] + 20, (k, out)
