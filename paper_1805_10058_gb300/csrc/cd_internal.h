@@ -83,6 +83,8 @@ struct Epi {
   T* rout;
   const double* lmax;  // per solve: largest eigenvalue estimate of D^{-1} A
   int step;
+  const T* dinv = nullptr;  // 1 / diag(A) per solve ([B][N]); kernels that do not read it
+                            // form the diagonal from the 1D band diagonals
 };
 
 // y = A w (mode 0) or y = b - A w (mode 1) on one level; optional per-solve partial dots
@@ -97,6 +99,8 @@ int launch_apply(int d, int m, int P, const T* bands /*M,A,S*/, const T* w, T* y
 // ([3][W]: M, A, S).
 void register_level(const void* bands_dev, int m, int P, int lo, int hi, const double* central);
 void unregister_level(const void* bands_dev);
+// FP64 levels: also a (hi, lo) FP32 split of the k-major bands, for the double-FP32 apply.
+void register_level_ff(const double* bands_dev, int m, int P);
 // 2D apply kernel: 2 = v3 (x_2 first, packed pairs; default), 1 = v2, 0 = v1.
 void set_apply_variant(int v);
 // 3D apply: 1 = streaming fused kernel (default), 0 = three banded passes (kept for checks).
@@ -112,6 +116,12 @@ int fp64_emulated();
 // (returns the chosen variant, 0 if none was tuned).  Not inside a stream capture.
 template <typename T>
 int tune_apply2d(int m, int P, const T* bands, const T* w, T* y, int B, Coef c, cudaStream_t s);
+
+// Autotuner of the 3D apply: times the streaming kernel against the three banded passes on
+// (m, P, B) and records the faster (returns 1 streaming, 2 passes).  Not inside a stream capture.
+template <typename T>
+int tune_apply3d(int m, int P, const T* bands, const T* w, T* y, int B, Coef c, T* scratch,
+                 cudaStream_t s);
 
 template <typename T>
 bool apply_can_fuse(int d, int m, int P, const T* bands, int B);

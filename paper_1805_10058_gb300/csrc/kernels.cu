@@ -525,20 +525,54 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel
 struct StencilHost {
   int m, P, lo, hi;
   double c[3][13];
+  float2* ffT;  // device: the level's k-major bands [3][2P+1][m] split into (hi, lo) FP32 pairs
 };
 static std::mutex g_stencil_mu;
 static std::unordered_map<const void*, StencilHost> g_stencils;
 
+__global__ void split_bands_kernel(int n, const double* __restrict__ src, float2* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float h = __double2float_rn(src[i]);
+    dst[i] = make_float2(h, __double2float_rn(src[i] - (double)h));
+  }
+}
+
 void register_level(const void* bands_dev, int m, int P, int lo, int hi, const double* central) {
-  StencilHost st{m, P, lo, hi, {}};
+  StencilHost st{m, P, lo, hi, {}, nullptr};
   for (int x = 0; x < 3; ++x)
     for (int k = 0; k < 2 * P + 1 && k < 13; ++k) st.c[x][k] = central[x * (2 * P + 1) + k];
   std::lock_guard<std::mutex> lk(g_stencil_mu);
+  auto it = g_stencils.find(bands_dev);
+  if (it != g_stencils.end() && it->second.ffT) cudaFree(it->second.ffT);
   g_stencils[bands_dev] = st;
+}
+// FP64 levels also get the (hi, lo) split of their k-major bands for the double-FP32 apply.
+void register_level_ff(const double* bands_dev, int m, int P) {
+  const int n = 3 * (2 * P + 1) * m;
+  float2* ff = nullptr;
+  if (cudaMalloc(&ff, sizeof(float2) * (size_t)n) != cudaSuccess) {
+    cudaGetLastError();
+    return;  // the double-FP32 apply then declines this level
+  }
+  split_bands_kernel<<<(n + 255) / 256, 256>>>(n, bands_dev + (size_t)3 * m * (2 * P + 1), ff);
+  count_launch();
+  std::lock_guard<std::mutex> lk(g_stencil_mu);
+  auto it = g_stencils.find(bands_dev);
+  if (it == g_stencils.end()) {
+    cudaFree(ff);
+    return;
+  }
+  if (it->second.ffT) cudaFree(it->second.ffT);
+  it->second.ffT = ff;
 }
 void unregister_level(const void* bands_dev) {
   std::lock_guard<std::mutex> lk(g_stencil_mu);
-  g_stencils.erase(bands_dev);
+  auto it = g_stencils.find(bands_dev);
+  if (it != g_stencils.end()) {
+    if (it->second.ffT) cudaFree(it->second.ffT);
+    g_stencils.erase(it);
+  }
 }
 static bool find_level(const void* bands_dev, StencilHost& out) {
   std::lock_guard<std::mutex> lk(g_stencil_mu);
@@ -1042,6 +1076,16 @@ static void launch_stream3d(int m, const T* bands, const StencilHost& sh, const 
   if (nblk) *nblk = grid.x * grid.y * nchunk;
 }
 
+// ---- autotuning table of the 3D apply: (precision bytes, m, P) -> 1 = streaming kernel,
+// 2 = three banded passes (0 = not tuned: the static rule, streaming for FP32 with P <= 4)
+static std::mutex g_tune3d_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned3d;
+static int tuned3d_variant(size_t es, int m, int P) {
+  std::lock_guard<std::mutex> lk(g_tune3d_mu);
+  auto it = g_tuned3d.find(std::make_tuple((int)es, m, P));
+  return it == g_tuned3d.end() ? 0 : it->second;
+}
+
 template <typename T>
 static bool try_stream3d(int m, int P, const T* bands, const T* w, T* y, const T* rhs, int mode,
                          int B, Coef c, double* dotp, int* nblk, const int* active, cudaStream_t s,
@@ -1056,6 +1100,7 @@ static bool try_stream3d(int m, int P, const T* bands, const T* w, T* y, const T
   } else {
     StencilHost sh;
     if (!g_use_stream3d || !find_level(bands, sh) || sh.P != P) return false;
+    if (tuned3d_variant(sizeof(T), m, P) == 2) return false;
     if (dotp && (long long)((m + 31) / 32) * ((m + 7) / 8) * ((m + 31) / 32) > kMaxPartials)
       return false;
     switch (P) {
@@ -1183,6 +1228,37 @@ __device__ __forceinline__ float2 ff_split(double v) {
   const float h = __double2float_rn(v);
   return make_float2(h, __double2float_rn(__dsub_rn(v, (double)h)));
 }
+// The same split by integer operations only (no FP64 or conversion instruction): hi = v
+// truncated to 24 significant bits, lo = the next 24 of the remaining 29 (truncated), so
+// hi + lo equals v to 48 bits.  Values below 2^-100 in magnitude (and their low parts below the
+// FP32 normal range) are flushed to zero: far below the rounding of any sum they enter here.
+__device__ __forceinline__ float2 ff_split_bits(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
+  const unsigned sign = hi32 & 0x80000000u;
+  const int ex = (int)((hi32 >> 20) & 0x7ffu);
+  const int exf = ex - 1023 + 127;
+  if (exf < 28 || exf > 254) return make_float2(0.f, 0.f);
+  const unsigned man = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+  const float h = __uint_as_float(sign | ((unsigned)exf << 23) | man);
+  const unsigned r = lo32 & 0x1fffffffu;  // v - h = r 2^(ex - 1075)
+  if (r == 0u) return make_float2(h, 0.f);
+  const int lz = __clz(r);                // leading one at bit 31 - lz
+  const int el = (31 - lz) + (ex - 1075) + 127;
+  if (el <= 0) return make_float2(h, 0.f);
+  const unsigned ml = (r << (lz + 1)) >> 9;  // the 23 bits after the leading one
+  return make_float2(h, __uint_as_float(sign | ((unsigned)el << 23) | ml));
+}
+// exact FP32 -> FP64 by integer operations (zero and FP32 subnormals give zero)
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0u) return 0.0;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex - 127u + 1023u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
 // acc += c * x (all double-FP32)
 __device__ __forceinline__ void ff_fma(float2& acc, float2 c, float2 x) {
   const float p = __fmul_rn(c.x, x.x);
@@ -1205,15 +1281,16 @@ __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
   return ff_norm(acc);
 }
 __device__ __forceinline__ double ff_to_double(float2 a) {
-  return __dadd_rn((double)a.x, (double)a.y);
+  return __dadd_rn(f2d_bits(a.x), f2d_bits(a.y));
 }
 
 template <int P, int TR>
 __global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
-    int m, const double* __restrict__ bandT, StencilFF cs, const double* __restrict__ w,
+    int m, const float2* __restrict__ bandF, StencilFF cs, const double* __restrict__ w,
     double* __restrict__ y, const double* __restrict__ rhs, int mode,
     const double* __restrict__ alpha, const double* __restrict__ beta,
-    const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp) {
+    const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
+    Epi<double> epi) {
   constexpr int W = 2 * P + 1, TC = 64, HR = TR + 2 * P, HC = TC + 2 * P;
   const int b = blockIdx.z;
   if (active && !active[b]) return;
@@ -1225,16 +1302,17 @@ __global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
   const int c0 = blockIdx.x * TC, r0 = blockIdx.y * TR;
   const float2 al = ff_split(alpha[b]), be = ff_split(beta[b]);
   const float2 ga = ff_split((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
-  const double* BM = bandT;
-  const double* BA = bandT + (size_t)W * m;
-  const double* BS = bandT + (size_t)2 * W * m;
+  const float2* BM = bandF;
+  const float2* BA = bandF + (size_t)W * m;
+  const float2* BS = bandF + (size_t)2 * W * m;
   // tile of w with halos, split once
   for (int idx = threadIdx.x; idx < 2 * HR * HC; idx += blockDim.x) {
     const int c = idx / (HR * HC), rem = idx - c * HR * HC;
     const int rr = rem / HC, cc = rem - rr * HC;
     const int row = r0 - P + rr, col = c0 - P + cc;
     float2 v = make_float2(0.f, 0.f);
-    if (row >= 0 && row < m && col >= 0 && col < m) v = ff_split(wb[(long long)c * m * m + (long long)row * m + col]);
+    if (row >= 0 && row < m && col >= 0 && col < m)
+      v = ff_split_bits(wb[(long long)c * m * m + (long long)row * m + col]);
     sw[idx] = v;
   }
   __syncthreads();
@@ -1254,9 +1332,9 @@ __global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
           cA = cs.c[1][k];
           cS = cs.c[2][k];
         } else {
-          cM = ff_split(BM[(size_t)k * m + j]);
-          cA = ff_split(BA[(size_t)k * m + j]);
-          cS = ff_split(BS[(size_t)k * m + j]);
+          cM = BM[(size_t)k * m + j];
+          cA = BA[(size_t)k * m + j];
+          cS = BS[(size_t)k * m + j];
         }
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
@@ -1283,7 +1361,8 @@ __global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
   }
   __syncthreads();
   // axis x_1: y_c = M1 PM_c + S1 PS_c + A1 PA_c
-  double acc = 0.0;
+  double acc = 0.0, ec1 = 0.0, ec2 = 0.0;
+  if (mode == 2) cheb_coef(epi.lmax[b], epi.step, ec1, ec2);
   for (int item = threadIdx.x; item < TR * TC; item += blockDim.x) {
     const int r = item / TC, cc = item - r * TC;
     const int i = r0 + r, j = c0 + cc;
@@ -1298,9 +1377,9 @@ __global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
         cA = cs.c[1][k];
         cS = cs.c[2][k];
       } else {
-        cM = ff_split(BM[(size_t)k * m + i]);
-        cA = ff_split(BA[(size_t)k * m + i]);
-        cS = ff_split(BS[(size_t)k * m + i]);
+        cM = BM[(size_t)k * m + i];
+        cA = BA[(size_t)k * m + i];
+        cS = BS[(size_t)k * m + i];
       }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -1311,6 +1390,11 @@ __global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
     }
     const long long o1 = (long long)b * N + (long long)i * m + j, o2 = o1 + (long long)m * m;
     double y1 = ff_to_double(ff_norm(yy[0])), y2 = ff_to_double(ff_norm(yy[1]));
+    if (mode == 2) {  // fused Chebyshev step with the stored 1 / diag(A)
+      cheb_epi(epi, o1, rhs[o1] - y1, epi.dinv[o1], ec1, ec2);
+      cheb_epi(epi, o2, rhs[o2] - y2, epi.dinv[o2], ec1, ec2);
+      continue;
+    }
     if (mode == 1) {
       y1 = rhs[o1] - y1;
       y2 = rhs[o2] - y2;
@@ -1354,8 +1438,7 @@ static bool launch_ff_P(int m, const double* bands, const StencilHost& sh, const
   cs.hi = sh.hi;
   dim3 grid((m + 63) / 64, (m + TR - 1) / TR, B);
   apply2d_ff_kernel<P, TR><<<grid, 256, ff_smem<P, TR>(), s>>>(
-      m, bands + (size_t)3 * m * (2 * P + 1), cs, w, y, rhs, mode, c.alpha, c.beta, c.gsc, active,
-      dotp);
+      m, sh.ffT, cs, w, y, rhs, mode, c.alpha, c.beta, c.gsc, active, dotp, g_epi<double>);
   count_launch();
   if (nblk) *nblk = grid.x * grid.y;
   return true;
@@ -1368,9 +1451,9 @@ int fp64_emulated() { return g_ff_inner || g_ff_forced; }
 static bool try_apply2d_ff(int m, int P, const double* bands, const double* w, double* y,
                            const double* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
                            const int* active, cudaStream_t s) {
-  if (mode == 2) return false;
+  if (mode == 2 && !g_epi<double>.dinv) return false;
   StencilHost sh;
-  if (!find_level(bands, sh) || sh.P != P) return false;
+  if (!find_level(bands, sh) || sh.P != P || !sh.ffT) return false;
   if (dotp && (long long)((m + 63) / 64) * ((m + 15) / 16) > kMaxPartials) return false;
   switch (P) {
     case 1: return launch_ff_P<1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
@@ -1432,7 +1515,7 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
   }
   if (d == 2) {
     if constexpr (sizeof(T) == 8) {
-      if (mode != 2 && fp64_emulated() &&
+      if (fp64_emulated() &&
           try_apply2d_ff(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
         return 0;
     }
@@ -1585,13 +1668,69 @@ int tune_apply2d(int m, int P, const T* bands, const T* w, T* y, int B, Coef c, 
   return bestv;
 }
 template int tune_apply2d<float>(int, int, const float*, const float*, float*, int, Coef, cudaStream_t);
+
+// Times the two 3D apply designs (the streaming kernel, where it exists for this precision and
+// P, and the three banded passes) on (m, P, B) with CUDA events on stream s and records the
+// faster; both compute y = A w, the passes in a different summation order.  Not inside a stream
+// capture.  Returns the chosen variant (1 streaming, 2 passes).
+template <typename T>
+int tune_apply3d(int m, int P, const T* bands, const T* w, T* y, int B, Coef c, T* scratch,
+                 cudaStream_t s) {
+  const auto key = std::make_tuple((int)sizeof(T), m, P);
+  {
+    std::lock_guard<std::mutex> lk(g_tune3d_mu);
+    auto it = g_tuned3d.find(key);
+    if (it != g_tuned3d.end()) return it->second;
+  }
+  if (sizeof(T) == 8 || P > 4 || !g_use_stream3d) {  // only the passes exist here
+    std::lock_guard<std::mutex> lk(g_tune3d_mu);
+    g_tuned3d[key] = 2;
+    return 2;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 0;
+  float best = 1e30f;
+  int bestv = 0;
+  for (int v = 1; v <= 2; ++v) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune3d_mu);
+      g_tuned3d[key] = v;
+    }
+    for (int rep = 0; rep < 2; ++rep)
+      launch_apply<T>(3, m, P, bands, w, y, nullptr, 0, B, c, nullptr, nullptr, nullptr, scratch, s);
+    cudaEventRecord(e0, s);
+    int bad = 0;
+    for (int rep = 0; rep < 3; ++rep)
+      bad |= launch_apply<T>(3, m, P, bands, w, y, nullptr, 0, B, c, nullptr, nullptr, nullptr,
+                             scratch, s);
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (bad == 0 && ms < best) {
+      best = ms;
+      bestv = v;
+    }
+  }
+  cudaGetLastError();
+  {
+    std::lock_guard<std::mutex> lk(g_tune3d_mu);
+    g_tuned3d[key] = bestv ? bestv : 2;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return bestv;
+}
+template int tune_apply3d<float>(int, int, const float*, const float*, float*, int, Coef,
+                                 float*, cudaStream_t);
+template int tune_apply3d<double>(int, int, const double*, const double*, double*, int, Coef,
+                                  double*, cudaStream_t);
 template int tune_apply2d<double>(int, int, const double*, const double*, double*, int, Coef, cudaStream_t);
 
 // Whether launch_apply supports mode 2 (fused smoother epilogue) for this level and batch.
 template <typename T>
 bool apply_can_fuse(int d, int m, int P, const T* bands, int B) {
   if (d == 3) return true;
-  if (sizeof(T) == 8 && fp64_emulated()) return false;  // the double-FP32 apply has no mode 2
   if (g_use_v2 < 1 || P < 1 || P > 6) return false;
   StencilHost sh;
   if (!find_level(bands, sh)) return false;

@@ -534,7 +534,7 @@ static void smooth_pre_fused(MgData& mg, int l, int B, const T* bl, T* X0, T* XB
   cheb_first_kernel<T><<<grid_for(N, B), 256, 0, s>>>(N, (const T*)lb.dinv, lm, bl, X0, (T*)lb.dv, 1,
                                                       active);
   count_launch();
-  Epi<T> e{X0, X0, XB, nullptr, nullptr, lm, 1};
+  Epi<T> e{X0, X0, XB, nullptr, nullptr, lm, 1, (const T*)lb.dinv};
   launch_apply<T>(mg.d, m, mg.P, level_bands<T>(mg, l), X0, nullptr, bl, 2, B, c, nullptr, nullptr,
                   active, scr, s, &e);
 }
@@ -546,10 +546,10 @@ static void smooth_post_fused(MgData& mg, int l, int B, const T* bl, const T* XB
   MgLevelBuf& lb = sizeof(T) == 8 ? mg.lv64[l] : mg.lv32[l];
   const double* lm = mg.lmax + (size_t)l * mg.B;
   const T* bands = level_bands<T>(mg, l);
-  Epi<T> e0{nullptr, XB, X0, (T*)lb.dv, (T*)lb.r, lm, 0};
+  Epi<T> e0{nullptr, XB, X0, (T*)lb.dv, (T*)lb.r, lm, 0, (const T*)lb.dinv};
   launch_apply<T>(mg.d, m, mg.P, bands, XB, nullptr, bl, 2, B, c, nullptr, nullptr, active, scr, s,
                   &e0);
-  Epi<T> e1{(const T*)lb.dv, X0, X0, nullptr, nullptr, lm, 1};
+  Epi<T> e1{(const T*)lb.dv, X0, X0, nullptr, nullptr, lm, 1, (const T*)lb.dinv};
   launch_apply<T>(mg.d, m, mg.P, bands, (const T*)lb.dv, nullptr, (const T*)lb.r, 2, B, c, nullptr,
                   nullptr, active, scr, s, &e1);
 }

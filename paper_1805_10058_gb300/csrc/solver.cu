@@ -834,6 +834,7 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   for (size_t l = 0; l < h->ml.size(); ++l) {
     register_level(h->bands64.as<double>() + h->boff[l], h->ml[l], P, interior[l].first,
                    interior[l].second, central[l].data());
+    if (d == 2) register_level_ff(h->bands64.as<double>() + h->boff[l], h->ml[l], P);
     register_level(h->bands32.as<float>() + h->boff[l], h->ml[l], P, interior[l].first,
                    interior[l].second, central[l].data());
   }
@@ -899,6 +900,20 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   if (h->opt.precond == CD_PC_MIM || h->opt.precond == CD_PC_WL) {
     cd_status st = ensure_ksmooth(h.get(), h->opt.precond);
     if (st != CD_OK) return st;
+  }
+  if (h->opt.autotune && d == 3) {  // pick the 3D apply design per level (FP32)
+    std::vector<double> ones(B, 1.0);
+    if (cudaMemcpyAsync(h->alpha.p, ones.data(), 8 * B, cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
+        cudaMemcpyAsync(h->beta.p, ones.data(), 8 * B, cudaMemcpyHostToDevice, h->s) != cudaSuccess) {
+      set_error("autotune set-up failed");
+      return CD_ECUDA;
+    }
+    h->dev_alpha = ones;
+    h->dev_beta = ones;
+    for (size_t l = 0; l < h->ml.size(); ++l)
+      tune_apply3d<float>(h->ml[l], P, bands_of<float>(h.get(), l), h->w32.p.as<float>(),
+                          h->w32.q.as<float>(), B, coef_of(h.get()),
+                          h->w32.apply_scratch.as<float>(), h->s);
   }
   if (h->opt.autotune && d == 2) {  // pick the 2D apply variant per level and precision
     std::vector<double> ones(B, 1.0);
