@@ -683,11 +683,22 @@ def run_serving(args):
 def run_profile_kernel(args):
     """A few launches of one kernel on its profiling case, for ncu (no timing): `apply` = the
     FP32 2D apply at p = 3, n = 256, batch 40 (four calls); `fd` = two FP32 FD-D applications
-    on the tensor cores at the same size (four passes each)."""
+    on the tensor cores at the same size (four passes each); `tail` = the kind of iteration that
+    dominates a sweep step: 16 solves at beta/alpha = 1e-6 and 1e6 (p = 3, n = 256, mixed
+    precision, which runs them in the FP64 inner group), multigrid FCG capped at 120 iterations."""
     import torch
     from paper_1805_10058_gb300 import curldiv as cdl
     B = 40
-    if args.profile_kernel == "apply":
+    if args.profile_kernel == "tail":
+        from paper_1805_10058_gb300 import inputs
+        B = 16
+        s = cdl.Solver(2, 3, N_INT, max_batch=B, precond=cdl.CD_PC_MG, rtol=1e-10, maxit=120)
+        b = torch.as_tensor(inputs.uniform_rhs(2, 3, N_INT, seed=0, nrhs=B).ravel(), device="cuda")
+        x, xl = torch.zeros_like(b), torch.zeros_like(b)
+        st, res = s.cd_solve_ext(b, x, xl, [1.0] * B, [1e-6] * 8 + [1e6] * 8, check=False)
+        assert st in (cdl.CD_OK, cdl.CD_NOT_CONVERGED), st
+        print("launches", cdl.cd_kernel_launches())
+    elif args.profile_kernel == "apply":
         s = cdl.Solver(2, 3, N_INT, max_batch=B, precond=cdl.CD_PC_NONE)
         w = torch.rand(B * s.N, dtype=torch.float32, device="cuda")
         y = torch.empty_like(w)
@@ -722,7 +733,7 @@ def main():
     ap.add_argument("--serving", action="store_true", help="serving-stream workload instead")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--workers", type=int, default=4)
-    ap.add_argument("--profile-kernel", choices=["apply", "fd"], default=None,
+    ap.add_argument("--profile-kernel", choices=["apply", "fd", "tail"], default=None,
                     help="a few launches of one kernel for ncu, no timing")
     args = ap.parse_args()
     if args.profile_kernel:

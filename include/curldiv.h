@@ -125,8 +125,8 @@ typedef struct {
                           rule is not limited by FP64 rounding of A x (at beta/alpha = 1e+-6
                           and n = 256 an FP64 evaluation bottoms out near 1e-8).  0: FP64
                           solution and residual.                                           */
-  int emulated_fp64;   /* 1 (default, with ext_residual): the FP64 inner Krylov solves of 2D
-                          problems apply the operator in double-FP32 arithmetic (about 48
+  int emulated_fp64;   /* 1 (default, with ext_residual and CD_PREC_FP32_IR): the FP64 inner
+                          Krylov solves of 2D problems apply the operator in double-FP32 (about 48
                           significant bits) on the FP32 pipe, several times the FP64 rate on
                           GB300; their inner tolerance is then floored at 1e-6 relative and the
                           double-FP64 outer residual restores the accuracy.  0: FP64 applies.  */

@@ -464,6 +464,11 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, double* x
   count_launch(4);
   vzero<double>(N, B, x, nullptr, h->s);
   const bool ext = h->opt.ext_residual != 0;
+  // 2D mixed precision: the FP64 inner solves apply the operator in double-FP32 on the FP32
+  // pipe (the double-FP64 outer residual corrects its coarser rounding).  CD_PREC_FP64 keeps
+  // FP64 arithmetic throughout.
+  const bool emu_inner = ext && h->opt.emulated_fp64 && h->d == 2 &&
+                         h->opt.precision != CD_PREC_FP64;
   double* xlo = ext ? h->xlo64.as<double>() : nullptr;
   if (ext) vzero<double>(N, B, xlo, nullptr, h->s);
   launch_dot<double>(b, b, N, B, h->part[1].as<double>(), nb, nullptr, h->s);
@@ -478,7 +483,7 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, double* x
              h->ir_rrprev.as<double>(), act, h->ir_status.as<int>(), h->ir_relres.as<double>(),
              h->ir_outer.as<int>(), h->ir_grp.as<int>(), h->ir_tol2.as<double>(),
              h->opt.rtol * h->opt.rtol, inner2, h->opt.max_outer, h->ir_inner_total.as<int>(),
-             h->opt.maxit, (ext && h->opt.emulated_fp64 && h->d == 2) ? 1e-12 : 1e-30, h->s);
+             h->opt.maxit, emu_inner ? 1e-12 : 1e-30, h->s);
     group_masks(B, act, h->ir_grp.as<int>(), m[0], m[1], m[2], h->cnt.as<int>(), h->s);
     CD_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->cnt.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
     CD_CUDA_OK(cudaStreamSynchronize(h->s));
@@ -506,10 +511,7 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, double* x
       // keeps the whole budget (the outer check stops a solve at maxit iterations in total).
       const int cap = (step == 0 || ext) ? h->opt.maxit
                                          : std::min({h->opt.maxit, h->opt.inner_maxit, 500});
-      // 2D: the inner FP64 solve applies the operator in double-FP32 on the FP32 pipe (the
-      // double-FP64 outer residual corrects its coarser rounding)
-      const bool emu = ext && h->opt.emulated_fp64 && h->d == 2;
-      set_fp64_emulated(emu ? 1 : 0);
+      set_fp64_emulated(emu_inner ? 1 : 0);
       cd_status st = run_pcg<double>(h, B, pc, tol2v, cap, m[g]);
       set_fp64_emulated(0);
       if (st != CD_OK) return st;
