@@ -258,6 +258,19 @@ def cpu_baseline_sample():
 
 
 # ------------------------------------------------------------------ our arm
+def alu_peak_tops(dev):
+    """Nominal FP32 operation rate of this GPU: SMs x 128 FP32 lanes x the maximum SM clock, one
+    FMA, add or multiply per lane per clock (a packed FFMA2 / FADD2 occupies two lanes)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return sms * 128 * mhz * 1e6 / 1e12, sms, mhz
+
+
 def fp64_peak_tflops(dev):
     """Measured FP64 peak of this GPU: cuBLAS DGEMM (torch.matmul, 4096^3, best of 5)."""
     import torch
@@ -532,7 +545,7 @@ def run_ours(args):
     fp64_tf = fp64_peak_tflops(dev)
     rl32 = {"bound": "hbm", "achieved": 2 * unknowns * 4 / t32 / 1e9, "peak": hbm, "unit": "GB/s",
             "traffic": None, "peak_kind": peak_kind,
-            "kernel": "apply2d_v3_kernel<float> (p=3, n=256, batch 40)", "launch_us": t32 * 1e6}
+            "kernel": "apply2d FP32 (autotuned v5/v3, p=3, n=256, batch 40)", "launch_us": t32 * 1e6}
     rl32["frac"] = rl32["achieved"] / hbm
     flops64 = 12 * (2 * p3 + 1) * unknowns
     rl64 = {"bound": "fp64", "achieved": flops64 / t64 / 1e12, "peak": fp64_tf, "unit": "TFLOP/s",
@@ -540,6 +553,30 @@ def run_ours(args):
             "kernel": "apply2d_v2_kernel<double> (p=3, n=256, batch 40)", "launch_us": t64 * 1e6,
             "hbm_gbs": 2 * unknowns * 8 / t64 / 1e9}
     rl64["frac"] = rl64["achieved"] / fp64_tf
+    # the step's dominant kernel (launch list of the tail: profiles/): the double-FP32 2D apply
+    # of the FP64 inner solves at the extreme ratios, on the 16 right-hand sides that stay active
+    # in a batch's tail.  Work = the plain double-FP32 form: 6 (2p+1) multiply-adds per unknown,
+    # 12 FP32 operations each (two-product with cross terms 4, two-sum 6, low-part sums 2).
+    Bff = 16
+    os.environ["CURLDIV_APPLY_KERNEL_FP64"] = "ff"
+    stff = torch.cuda.Stream(dev)
+    sff = cdl.Solver(2, p3, N_INT, max_batch=Bff, precond=cdl.CD_PC_NONE, autotune=0,
+                     stream=stff.cuda_stream)
+    os.environ.pop("CURLDIV_APPLY_KERNEL_FP64", None)
+    tff = time_apply(sff, stff, flush, Bff, torch.float64, np.ones(Bff), np.full(Bff, 1e6))
+    sff.close()
+    alu_tops, n_sm, sm_mhz = alu_peak_tops(dev)
+    ops_ff = 72 * (2 * p3 + 1) * Bff * s3.N
+    rlff = {"bound": "alu", "achieved": ops_ff / tff / 1e12, "peak": alu_tops, "unit": "TOP/s",
+            "traffic": None,
+            "peak_kind": f"nominal FP32 lanes x clock: {n_sm} SMs x 128 x {sm_mhz:.0f} MHz",
+            "kernel": f"apply2d_ff2_kernel<3> (double-FP32 apply, p=3, n=256, batch {Bff})",
+            "launch_us": tff * 1e6, "ops_per_launch": ops_ff,
+            "ops_definition": "72 (2p+1) FP32 operations per unknown (the plain double-FP32 "
+                              "sum-factorised form)",
+            "fp64_equiv_tflops": 12 * (2 * p3 + 1) * Bff * s3.N / tff / 1e12,
+            "hbm_gbs": 2 * Bff * s3.N * 8 / tff / 1e9}
+    rlff["frac"] = rlff["achieved"] / alu_tops
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -568,10 +605,11 @@ def run_ours(args):
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 2 * h2d,
                         "definition": "pinned host b -> device, cd_solve_ext, x and x_lo -> pinned host, "
                                       "wall time, converged solves counted"},
-                "roofline": rl64 if args.roofline_kernel == "fp64" else rl32,
-                "roofline_other": rl32 if args.roofline_kernel == "fp64" else rl64,
-                "roofline_choice": "kernel named by --roofline-kernel; the step's launch list is "
-                                   "summarised under profiles/",
+                "roofline": {"ff": rlff, "fp64": rl64, "fp32": rl32}[args.roofline_kernel],
+                "roofline_other": [r for k, r in (("ff", rlff), ("fp32", rl32), ("fp64", rl64))
+                                   if k != args.roofline_kernel],
+                "roofline_choice": "kernel named by --roofline-kernel (default: the step's dominant "
+                                   "kernel in its launch list, summarised under profiles/)",
                 "gpu_launches": int(launches),
                 "clocks": clk}
         cfgs = [c for c in args.configs.split(",") if c]
@@ -685,7 +723,8 @@ def run_profile_kernel(args):
     FP32 2D apply at p = 3, n = 256, batch 40 (four calls); `fd` = two FP32 FD-D applications
     on the tensor cores at the same size (four passes each); `tail` = the kind of iteration that
     dominates a sweep step: 16 solves at beta/alpha = 1e-6 and 1e6 (p = 3, n = 256, mixed
-    precision, which runs them in the FP64 inner group), multigrid FCG capped at 120 iterations."""
+    precision, which runs them in the FP64 inner group), multigrid FCG capped at 120 iterations;
+    `ff` = the double-FP32 2D apply of those inner solves at p = 3, n = 256, batch 16."""
     import torch
     from paper_1805_10058_gb300 import curldiv as cdl
     B = 40
@@ -698,8 +737,16 @@ def run_profile_kernel(args):
         st, res = s.cd_solve_ext(b, x, xl, [1.0] * B, [1e-6] * 8 + [1e6] * 8, check=False)
         assert st in (cdl.CD_OK, cdl.CD_NOT_CONVERGED), st
         print("launches", cdl.cd_kernel_launches())
+    elif args.profile_kernel == "ff":
+        os.environ["CURLDIV_APPLY_KERNEL_FP64"] = "ff"
+        B = 16
+        s = cdl.Solver(2, 3, N_INT, max_batch=B, precond=cdl.CD_PC_NONE, autotune=0)
+        w = torch.rand(B * s.N, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(w)
+        for _ in range(4):
+            s.cd_apply(w, y, [1.0] * B, [1e6] * B)
     elif args.profile_kernel == "apply":
-        s = cdl.Solver(2, 3, N_INT, max_batch=B, precond=cdl.CD_PC_NONE)
+        s = cdl.Solver(2, 3, N_INT, max_batch=B, precond=cdl.CD_PC_NONE, autotune=0)
         w = torch.rand(B * s.N, dtype=torch.float32, device="cuda")
         y = torch.empty_like(w)
         for _ in range(4):
@@ -723,7 +770,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--precond", default="mg", choices=["mg", "mim", "fdd", "none"])
-    ap.add_argument("--roofline-kernel", default="fp64", choices=["fp64", "fp32"],
+    ap.add_argument("--roofline-kernel", default="ff", choices=["ff", "fp64", "fp32"],
                     help="which operator apply the roofline key reports (the step's dominant one)")
     ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -733,7 +780,7 @@ def main():
     ap.add_argument("--serving", action="store_true", help="serving-stream workload instead")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--workers", type=int, default=4)
-    ap.add_argument("--profile-kernel", choices=["apply", "fd", "tail"], default=None,
+    ap.add_argument("--profile-kernel", choices=["apply", "fd", "tail", "ff"], default=None,
                     help="a few launches of one kernel for ncu, no timing")
     args = ap.parse_args()
     if args.profile_kernel:

@@ -28,7 +28,7 @@
  *
  * Errors: every entry point returns a cd_status and never throws or aborts
  * across the ABI.  CD_EINVAL: bad dimension (d not 2 or 3, p < 1, n < 1,
- * m < 2), non-finite or non-positive parameter, NULL pointer, nrhs < 1 or above
+ * m < 2, d m^d >= 2^31), non-finite or non-positive parameter, NULL pointer, nrhs < 1 or above
  * the handle's batch capacity.  CD_ECUDA: a CUDA call failed (the text is
  * available from cd_last_error).  CD_NOT_CONVERGED: maxit reached; x holds the
  * last iterate and cd_result its residual.  CD_BREAKDOWN: a Krylov denominator
@@ -113,12 +113,13 @@ typedef struct {
                                 Krylov solve is FP64 (default 1e4)                 */
   int fd_tensor_cores; /* FP32 FD transforms on tcgen05 (TF32 operands, FP32
                           accumulation; the Krylov method is then flexible) (1)   */
-  int autotune;        /* time the tilings of the FP32 2D apply for this shape at
-                          cd_create and keep the fastest (1).  Tilings give
-                          identical apply outputs; the fused dot partials are
-                          grouped by tile, so a solve's last bits can depend on
-                          the tiling, which is chosen once per (precision, m, p)
-                          and process (solves stay bit-identical within it)      */
+  int autotune;        /* time the FP32 2D apply kernels (folded-stencil tiles and two
+                          tilings of the packed-pair kernel) and the 3D apply designs
+                          for this shape at cd_create and keep the fastest (1).  The
+                          kernels agree to FP32 rounding, not bit for bit, so a solve's
+                          last bits can depend on the choice, which is made once per
+                          (precision, m, p) and process (solves stay bit-identical
+                          within it)                                               */
   int ext_residual;    /* 1 (default): the outer loop keeps the solution as an unevaluated
                           sum x_hi + x_lo of two FP64 vectors and evaluates b - A x in
                           double-FP64 arithmetic (about 106 significant bits), so the stopping

@@ -22,6 +22,7 @@
 #include <unordered_map>
 
 #include "cd_internal.h"
+#include "ffmath.h"
 
 namespace cd {
 
@@ -65,6 +66,22 @@ __device__ __forceinline__ void cheb_coef(double lmax, int step, double& c1, dou
   }
   c1 = rho * rho_prev;
   c2 = 2.0 * rho / de;
+}
+
+// The same coefficients computed once per CTA (thread 0, FP64) and shared.  GB300's FP64 pipe
+// runs at 1/64 of the FP32 rate, so a per-thread FP64 recurrence with divisions costs more than
+// a whole FP32 stencil.  Every thread of the CTA must reach this call.
+__device__ __forceinline__ void cheb_coef_cta(double lmax, int step, double& c1, double& c2) {
+  __shared__ double s_cc[2];
+  if (threadIdx.x == 0) {
+    double a, b;
+    cheb_coef(lmax, step, a, b);
+    s_cc[0] = a;
+    s_cc[1] = b;
+  }
+  __syncthreads();
+  c1 = s_cc[0];
+  c2 = s_cc[1];
 }
 
 template <typename T>
@@ -284,7 +301,7 @@ __global__ void __launch_bounds__(256, 2) apply2d_v2_kernel(
   T ec1 = 0, ec2 = 0;
   if (mode == 2) {
     double c1, c2;
-    cheb_coef(epi.lmax[b], epi.step, c1, c2);
+    cheb_coef_cta(epi.lmax[b], epi.step, c1, c2);
     ec1 = T(c1);
     ec2 = T(c2);
   }
@@ -456,7 +473,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel
   T ec1 = 0, ec2 = 0;
   if (mode == 2) {
     double c1, c2;
-    cheb_coef(epi.lmax[b], epi.step, c1, c2);
+    cheb_coef_cta(epi.lmax[b], epi.step, c1, c2);
     ec1 = T(c1);
     ec2 = T(c2);
   }
@@ -719,6 +736,315 @@ static bool try_apply2d_v2(int m, int P, const T* bands, const T* w, T* y, const
   }
 }
 
+// ------------------------------------------------------------------ 2D FP32 apply, v5
+// The FP32 operator apply on the tile layout of the packed double-FP32 kernel: the input tile
+// with its halo is staged once in shared memory by coalesced loads (w1, w2 interleaved as
+// float2), the x_2 pass runs one halo row per lane (folded symmetric / skew interior stencils,
+// FFMA2 on the component pair), the x_1 pass one column per lane; both shared-memory arrays
+// have an odd row stride in 8-byte slots, so both passes are free of bank conflicts.
+template <int P>
+struct V5Tile {
+  static constexpr int W = 2 * P + 1;
+  static constexpr int TC = 32;
+  static constexpr int TR = P <= 4 ? 24 : 20;
+  static constexpr int HR = TR + 2 * P;           // <= 32
+  static constexpr int HC = TC + 2 * P;
+  static constexpr int HCP = HC | 1;              // odd row strides (8-byte slots)
+  static constexpr int TCP = TC + 1;
+  static constexpr int NC = 4;
+  static constexpr int RS = TR / 4;
+  // input tile | intermediates | band rows of the tile's columns (boundary tiles); the band rows
+  // of the tile's rows reuse the input tile's space in the x_1 pass
+  static constexpr size_t off_mid = sizeof(float2) * HR * HCP;
+  static constexpr size_t off_col = off_mid + sizeof(float2) * 3 * HR * TCP;
+  static constexpr size_t smem = off_col + sizeof(float) * 3 * W * TC;
+  static_assert(sizeof(float) * 3 * W * TR <= off_mid, "row coefficients fit the input tile");
+};
+
+__device__ __forceinline__ float2 bc2(float c) { return make_float2(c, c); }
+
+__device__ __forceinline__ void v5_emit(float2 yy, int i, int j, long long o1, long long o2, int mode,
+                                        int m, int P, const float* __restrict__ BM,
+                                        const float* __restrict__ BS, float al, float be,
+                                        const float* __restrict__ w, float* __restrict__ y,
+                                        const float* __restrict__ rhs, const Epi<float>& epi,
+                                        float ec1, float ec2, const double* dotp, double& acc) {
+  float y1 = yy.x, y2 = yy.y;
+  if (mode == 2) {
+    const float Mi = BM[(size_t)P * m + i], Si = BS[(size_t)P * m + i];
+    const float Mj = BM[(size_t)P * m + j], Sj = BS[(size_t)P * m + j];
+    cheb_epi(epi, o1, rhs[o1] - y1, inv_diag2(be, Si, Mj, al, Mi, Sj), ec1, ec2);
+    cheb_epi(epi, o2, rhs[o2] - y2, inv_diag2(al, Si, Mj, be, Mi, Sj), ec1, ec2);
+    return;
+  }
+  if (mode == 1) {
+    y1 = rhs[o1] - y1;
+    y2 = rhs[o2] - y2;
+    if (dotp) acc += (double)y1 * (double)y1 + (double)y2 * (double)y2;
+  } else if (dotp) {
+    acc += (double)w[o1] * (double)y1 + (double)w[o2] * (double)y2;
+  }
+  y[o1] = y1;
+  y[o2] = y2;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128, P <= 4 ? 4 : 3) apply2d_v5_kernel(
+    int m, const float* __restrict__ bandT, Stencil<float> cs, const float* __restrict__ w,
+    float* __restrict__ y, const float* __restrict__ rhs, int mode,
+    const double* __restrict__ alpha, const double* __restrict__ beta,
+    const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
+    Epi<float> epi) {
+  using G = V5Tile<P>;
+  constexpr int W = G::W, TC = G::TC, TR = G::TR, HR = G::HR, HC = G::HC, HCP = G::HCP;
+  constexpr int TCP = G::TCP, NC = G::NC, RS = G::RS;
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sIn = reinterpret_cast<float2*>(smem_raw);                // [HR][HCP] (w1, w2)
+  float2* sMid = reinterpret_cast<float2*>(smem_raw + G::off_mid);  // [3][HR][TCP] PM, PS, PA
+  float* sCol = reinterpret_cast<float*>(smem_raw + G::off_col);    // [3][W][TC]
+  float* sRow = reinterpret_cast<float*>(smem_raw);                 // [3][W][TR] (x_1 pass)
+  const long long N = 2LL * m * m;
+  const float* wb = w + (long long)b * N;
+  const int c0 = blockIdx.x * TC, r0 = blockIdx.y * TR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool bcol = c0 < cs.lo || c0 + TC > cs.hi;
+  const bool brow = r0 < cs.lo || r0 + TR > cs.hi;
+  {  // every load of the tile in flight before the first store (one memory latency per tile)
+    constexpr int NE = (HR * HC + 127) / 128;
+    float2 v[NE];
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+      const int idx = threadIdx.x + 128 * t;
+      const int rr = idx / HC, cc = idx - rr * HC;
+      const int row = r0 - P + rr, col = c0 - P + cc;
+      v[t] = make_float2(0.f, 0.f);
+      if (idx < HR * HC && row >= 0 && row < m && col >= 0 && col < m) {
+        const long long o = (long long)row * m + col;
+        v[t] = make_float2(wb[o], wb[(long long)m * m + o]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+      const int idx = threadIdx.x + 128 * t;
+      const int rr = idx / HC, cc = idx - rr * HC;
+      if (idx < HR * HC) sIn[rr * HCP + cc] = v[t];
+    }
+  }
+  if (bcol) {
+    constexpr int NK = (3 * W * TC + 127) / 128;
+    float v[NK];
+#pragma unroll
+    for (int t = 0; t < NK; ++t) {
+      const int idx = threadIdx.x + 128 * t;
+      const int xk = idx / TC, cc = idx - xk * TC;
+      v[t] = idx < 3 * W * TC && c0 + cc < m ? bandT[(size_t)xk * m + c0 + cc] : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < NK; ++t)
+      if (threadIdx.x + 128 * t < 3 * W * TC) sCol[threadIdx.x + 128 * t] = v[t];
+  }
+  __shared__ float s_par[3];  // alpha, beta, gamma in FP32, converted once per CTA
+  if (threadIdx.x == 0) {
+    s_par[0] = float(alpha[b]);
+    s_par[1] = float(beta[b]);
+    s_par[2] = float((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
+  }
+  __syncthreads();
+  const float al = s_par[0], be = s_par[1], ga = s_par[2];
+  // ---- axis x_2: lane = halo row
+  if (lane < HR) {
+    const int q = lane, row = r0 - P + q;
+    const bool rowok = row >= 0 && row < m;
+    for (int g = warp; g < TC / NC; g += 4) {
+      const int j0 = c0 + g * NC;
+      if (rowok && j0 < m && j0 >= cs.lo && j0 + NC - 1 < cs.hi) {
+        float2 x[NC + 2 * P];
+#pragma unroll
+        for (int t = 0; t < NC + 2 * P; ++t) x[t] = sIn[q * HCP + g * NC + t];
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+          float2 tM = __fmul2_rn(bc2(cs.c[0][P]), x[u + P]);
+          float2 tS = __fmul2_rn(bc2(cs.c[2][P]), x[u + P]);
+          float2 tA = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int t = 1; t <= P; ++t) {
+            const float2 sp = __fadd2_rn(x[u + P - t], x[u + P + t]);
+            const float2 dp = __ffma2_rn(x[u + P - t], bc2(-1.f), x[u + P + t]);
+            tM = __ffma2_rn(bc2(cs.c[0][P + t]), sp, tM);
+            tS = __ffma2_rn(bc2(cs.c[2][P + t]), sp, tS);
+            tA = __ffma2_rn(bc2(cs.c[1][P + t]), dp, tA);
+          }
+          const int cc = g * NC + u;
+          sMid[(0 * HR + q) * TCP + cc] = __fmul2_rn(make_float2(al, be), tS);  // feeds M1
+          sMid[(1 * HR + q) * TCP + cc] = __fmul2_rn(make_float2(be, al), tM);  // feeds S1
+          sMid[(2 * HR + q) * TCP + cc] = __fmul2_rn(bc2(ga), make_float2(tA.y, tA.x));
+        }
+      } else {  // boundary columns (band rows staged in shared memory) or outside the domain
+#pragma unroll 1
+        for (int u = 0; u < NC; ++u) {
+          const int cc = g * NC + u;
+          float2 tM = make_float2(0.f, 0.f), tS = tM, tA = tM;
+          if (rowok && c0 + cc < m) {
+#pragma unroll 1
+            for (int k = 0; k < W; ++k) {
+              const float2 xv = sIn[q * HCP + cc + k];
+              tM = __ffma2_rn(bc2(sCol[(0 * W + k) * TC + cc]), xv, tM);
+              tA = __ffma2_rn(bc2(sCol[(1 * W + k) * TC + cc]), xv, tA);
+              tS = __ffma2_rn(bc2(sCol[(2 * W + k) * TC + cc]), xv, tS);
+            }
+          }
+          sMid[(0 * HR + q) * TCP + cc] = __fmul2_rn(make_float2(al, be), tS);
+          sMid[(1 * HR + q) * TCP + cc] = __fmul2_rn(make_float2(be, al), tM);
+          sMid[(2 * HR + q) * TCP + cc] = __fmul2_rn(bc2(ga), make_float2(tA.y, tA.x));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (brow) {
+    constexpr int NK = (3 * W * TR + 127) / 128;
+    float v[NK];
+#pragma unroll
+    for (int t = 0; t < NK; ++t) {
+      const int idx = threadIdx.x + 128 * t;
+      const int xk = idx / TR, rr = idx - xk * TR;
+      v[t] = idx < 3 * W * TR && r0 + rr < m ? bandT[(size_t)xk * m + r0 + rr] : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < NK; ++t)
+      if (threadIdx.x + 128 * t < 3 * W * TR) sRow[threadIdx.x + 128 * t] = v[t];
+    __syncthreads();
+  }
+  // ---- axis x_1: lane = column, RS rows per warp
+  double acc = 0.0;
+  float ec1 = 0.f, ec2 = 0.f;
+  if (mode == 2) {
+    double c1, c2;
+    cheb_coef_cta(epi.lmax[b], epi.step, c1, c2);
+    ec1 = float(c1);
+    ec2 = float(c2);
+  }
+  const float* BM = bandT;
+  const float* BS = bandT + (size_t)2 * W * m;
+  const int cc = lane, j = c0 + cc, rb = warp * RS;
+  if (j < m) {
+    if (r0 + rb >= cs.lo && r0 + rb + RS - 1 < cs.hi) {
+      float2 yy[RS];
+#pragma unroll
+      for (int r = 0; r < RS; ++r) yy[r] = make_float2(0.f, 0.f);
+#pragma unroll 1
+      for (int band = 0; band < 2; ++band) {  // M on PM, S on PS (symmetric)
+        float2 v[RS + 2 * P];
+#pragma unroll
+        for (int t = 0; t < RS + 2 * P; ++t) v[t] = sMid[(band * HR + rb + t) * TCP + cc];
+        float cf[P + 1];
+#pragma unroll
+        for (int t = 0; t <= P; ++t) cf[t] = band == 0 ? cs.c[0][P + t] : cs.c[2][P + t];
+#pragma unroll
+        for (int r = 0; r < RS; ++r) {
+          yy[r] = __ffma2_rn(bc2(cf[0]), v[r + P], yy[r]);
+#pragma unroll
+          for (int t = 1; t <= P; ++t)
+            yy[r] = __ffma2_rn(bc2(cf[t]), __fadd2_rn(v[r + P - t], v[r + P + t]), yy[r]);
+        }
+      }
+      {  // A on PA (skew)
+        float2 v[RS + 2 * P];
+#pragma unroll
+        for (int t = 0; t < RS + 2 * P; ++t) v[t] = sMid[(2 * HR + rb + t) * TCP + cc];
+#pragma unroll
+        for (int r = 0; r < RS; ++r)
+#pragma unroll
+          for (int t = 1; t <= P; ++t)
+            yy[r] = __ffma2_rn(bc2(cs.c[1][P + t]),
+                               __ffma2_rn(v[r + P - t], bc2(-1.f), v[r + P + t]), yy[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < RS; ++r) {
+        const int i = r0 + rb + r;
+        const long long o1 = (long long)b * N + (long long)i * m + j;
+        v5_emit(yy[r], i, j, o1, o1 + (long long)m * m, mode, m, P, BM, BS, al, be, w, y, rhs, epi,
+                ec1, ec2, dotp, acc);
+      }
+    } else {  // boundary rows (band rows staged in shared memory)
+#pragma unroll 1
+      for (int r = 0; r < RS; ++r) {
+        const int i = r0 + rb + r;
+        if (i >= m) break;
+        float2 yy = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int band = 0; band < 3; ++band) {
+          const int x = band == 0 ? 0 : band == 1 ? 2 : 1;
+#pragma unroll 1
+          for (int k = 0; k < W; ++k)
+            yy = __ffma2_rn(bc2(sRow[(x * W + k) * TR + rb + r]), sMid[(band * HR + rb + r + k) * TCP + cc], yy);
+        }
+        const long long o1 = (long long)b * N + (long long)i * m + j;
+        v5_emit(yy, i, j, o1, o1 + (long long)m * m, mode, m, P, BM, BS, al, be, w, y, rhs, epi,
+                ec1, ec2, dotp, acc);
+      }
+    }
+  }
+  if (dotp) {
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0)
+      dotp[(size_t)b * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+template <int P>
+static void set_v5_attr() {
+  cudaFuncSetAttribute(apply2d_v5_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)V5Tile<P>::smem);
+}
+
+static bool stencil_folds(const StencilHost& sh) {
+  const int P = sh.P;
+  for (int t = 1; t <= P; ++t) {
+    if (sh.c[0][P - t] != sh.c[0][P + t] || sh.c[2][P - t] != sh.c[2][P + t]) return false;
+    if (sh.c[1][P - t] != -sh.c[1][P + t]) return false;
+  }
+  return sh.c[1][P] == 0.0;
+}
+
+template <int P>
+static bool launch_v5_P(int m, const float* bands, const StencilHost& sh, const float* w, float* y,
+                        const float* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                        const int* active, cudaStream_t s) {
+  using G = V5Tile<P>;
+  Stencil<float> cs;
+  for (int x = 0; x < 3; ++x)
+    for (int k = 0; k < 13; ++k) cs.c[x][k] = k < 2 * P + 1 ? (float)sh.c[x][k] : 0.f;
+  cs.lo = sh.lo;
+  cs.hi = sh.hi;
+  dim3 grid((m + G::TC - 1) / G::TC, (m + G::TR - 1) / G::TR, B);
+  if (dotp && (long long)grid.x * grid.y > kMaxPartials) return false;
+  apply2d_v5_kernel<P><<<grid, 128, G::smem, s>>>(m, bands + (size_t)3 * m * (2 * P + 1), cs, w, y,
+                                                  rhs, mode, c.alpha, c.beta, c.gsc, active, dotp,
+                                                  g_epi<float>);
+  count_launch();
+  if (nblk) *nblk = grid.x * grid.y;
+  return true;
+}
+
+static bool try_apply2d_v5(int m, int P, const float* bands, const float* w, float* y,
+                           const float* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                           const int* active, cudaStream_t s) {
+  StencilHost sh;
+  if (!find_level(bands, sh) || sh.P != P || !stencil_folds(sh)) return false;
+  switch (P) {
+    case 1: return launch_v5_P<1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 2: return launch_v5_P<2>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 3: return launch_v5_P<3>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 4: return launch_v5_P<4>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 5: return launch_v5_P<5>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    case 6: return launch_v5_P<6>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
+    default: return false;
+  }
+}
+
 template <typename T, int P, int TR>
 static void set_v2_attr() {
   cudaFuncSetAttribute(apply2d_v2_kernel<T, P, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -905,7 +1231,7 @@ __global__ void __launch_bounds__(32 * T2, 2) apply3d_stream_kernel(
   T ec1 = 0, ec2 = 0;
   if (mode == 2) {
     double c1, c2;
-    cheb_coef(epi.lmax[b], epi.step, c1, c2);
+    cheb_coef_cta(epi.lmax[b], epi.step, c1, c2);
     ec1 = T(c1);
     ec2 = T(c2);
   }
@@ -1137,7 +1463,7 @@ __global__ void __launch_bounds__(256) post3d_kernel(long long N, const T* __res
   T ec1 = 0, ec2 = 0;
   if (mode == 2) {
     double c1, c2;
-    cheb_coef(epi.lmax[b], epi.step, c1, c2);
+    cheb_coef_cta(epi.lmax[b], epi.step, c1, c2);
     ec1 = T(c1);
     ec2 = T(c2);
   }
@@ -1200,13 +1526,15 @@ static int tuned_variant(size_t es, int m, int P, int /*B*/) {
   auto it = g_tuned.find(std::make_tuple((int)es, m, P));
   return it == g_tuned.end() ? 0 : it->second;
 }
-static int g_use_v2 = 2;  // 2: v3 kernel, 1: v2 kernel, 0: v1 kernel
+static int g_use_v2 = 2;  // 2: v5 then v3 kernel (FP32), 3: v3 only, 1: v2 kernel, 0: v1 kernel
 void set_apply_variant(int v) { g_use_v2 = v; }
 static int g_fp64_v3 = 0;    // FP64 2D apply: 0 = v2 (default), 1 = v3 (8 rows per tile)
-static int g_ff_forced = 0;  // 2: every FP64 2D apply in double-FP32 (kernel checks)
+static int g_ff_forced = 0;  // 1: every FP64 2D apply in double-FP32 (kernel checks)
+static int g_ff_kernel = 2;  // double-FP32 2D apply: 2 = packed folded kernel, 1 = plain kernel
 void set_apply_fp64_variant(int v) {
   g_fp64_v3 = v == 1;
-  g_ff_forced = v == 2;
+  g_ff_forced = v == 2 || v == 3 || v == 4;
+  g_ff_kernel = v == 4 ? 1 : 2;
 }
 void set_apply3d_variant(int v) { g_use_stream3d = v; }
 
@@ -1227,37 +1555,6 @@ struct StencilFF {
 __device__ __forceinline__ float2 ff_split(double v) {
   const float h = __double2float_rn(v);
   return make_float2(h, __double2float_rn(__dsub_rn(v, (double)h)));
-}
-// The same split by integer operations only (no FP64 or conversion instruction): hi = v
-// truncated to 24 significant bits, lo = the next 24 of the remaining 29 (truncated), so
-// hi + lo equals v to 48 bits.  Values below 2^-100 in magnitude (and their low parts below the
-// FP32 normal range) are flushed to zero: far below the rounding of any sum they enter here.
-__device__ __forceinline__ float2 ff_split_bits(double v) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  const unsigned hi32 = (unsigned)(u >> 32), lo32 = (unsigned)u;
-  const unsigned sign = hi32 & 0x80000000u;
-  const int ex = (int)((hi32 >> 20) & 0x7ffu);
-  const int exf = ex - 1023 + 127;
-  if (exf < 28 || exf > 254) return make_float2(0.f, 0.f);
-  const unsigned man = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
-  const float h = __uint_as_float(sign | ((unsigned)exf << 23) | man);
-  const unsigned r = lo32 & 0x1fffffffu;  // v - h = r 2^(ex - 1075)
-  if (r == 0u) return make_float2(h, 0.f);
-  const int lz = __clz(r);                // leading one at bit 31 - lz
-  const int el = (31 - lz) + (ex - 1075) + 127;
-  if (el <= 0) return make_float2(h, 0.f);
-  const unsigned ml = (r << (lz + 1)) >> 9;  // the 23 bits after the leading one
-  return make_float2(h, __uint_as_float(sign | ((unsigned)el << 23) | ml));
-}
-// exact FP32 -> FP64 by integer operations (zero and FP32 subnormals give zero)
-__device__ __forceinline__ double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ex = (u >> 23) & 0xffu;
-  if (ex == 0u) return 0.0;
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(ex - 127u + 1023u) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)d);
 }
 // acc += c * x (all double-FP32)
 __device__ __forceinline__ void ff_fma(float2& acc, float2 c, float2 x) {
@@ -1362,7 +1659,7 @@ __global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
   __syncthreads();
   // axis x_1: y_c = M1 PM_c + S1 PS_c + A1 PA_c
   double acc = 0.0, ec1 = 0.0, ec2 = 0.0;
-  if (mode == 2) cheb_coef(epi.lmax[b], epi.step, ec1, ec2);
+  if (mode == 2) cheb_coef_cta(epi.lmax[b], epi.step, ec1, ec2);
   for (int item = threadIdx.x; item < TR * TC; item += blockDim.x) {
     const int r = item / TC, cc = item - r * TC;
     const int i = r0 + r, j = c0 + cc;
@@ -1444,6 +1741,398 @@ static bool launch_ff_P(int m, const double* bands, const StencilHost& sh, const
   return true;
 }
 
+// ------------------------------------------------------------------ 2D apply in double-FP32, v2
+// The same operator and arithmetic type as apply2d_ff_kernel, rebuilt for issue rate:
+//  * the two components of a grid point travel together as packed pairs, so every double-FP32
+//    step is a packed FP32 instruction (FFMA2 / FADD2 / FMUL2) acting on (w1, w2) at once;
+//  * in the interior, where the bands equal their central rows, the symmetric M and S and the
+//    skew A are applied in folded form: c_0 x_0 + sum_t c_t (x_{-t} +- x_{+t}), the pair sums
+//    shared by M and S along x_2 (about 2/3 of the double-FP32 multiply-adds of the plain form);
+//  * shared memory rows have an odd number of 16-byte slots, so the column-wise x_2 pass (lanes
+//    = rows) and the row-wise x_1 pass (lanes = columns) are both free of bank conflicts.
+// Tile: TR = 24 (P <= 4) or 20 output rows x 32 columns per CTA of 128 threads; the x_2 pass
+// covers the TR + 2P <= 32 rows of the halo, one row per lane.
+struct FF2 {  // two double-FP32 numbers: (h.x + l.x, h.y + l.y)
+  float2 h, l;
+};
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {  // a - b, one rounding
+  return __ffma2_rn(b, f2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, f2(-1.f, -1.f)); }
+// acc += c * x, c = ch + cl per lane
+__device__ __forceinline__ void ff2_fma(FF2& acc, float2 ch, float2 cl, const FF2& x) {
+  const float2 p = __fmul2_rn(ch, x.h);
+  float2 e = __ffma2_rn(ch, x.h, neg2(p));
+  e = __ffma2_rn(ch, x.l, e);
+  e = __ffma2_rn(cl, x.h, e);
+  const float2 sm = __fadd2_rn(acc.h, p);
+  const float2 bb = sub2(sm, acc.h);
+  const float2 er = __fadd2_rn(sub2(acc.h, sub2(sm, bb)), sub2(p, bb));
+  acc.l = __fadd2_rn(acc.l, __fadd2_rn(er, e));
+  acc.h = sm;
+}
+// a + b and a - b (two-sum of the high parts; low parts added)
+__device__ __forceinline__ FF2 ff2_add(const FF2& a, const FF2& b) {
+  const float2 sm = __fadd2_rn(a.h, b.h);
+  const float2 bb = sub2(sm, a.h);
+  const float2 er = __fadd2_rn(sub2(a.h, sub2(sm, bb)), sub2(b.h, bb));
+  return FF2{sm, __fadd2_rn(__fadd2_rn(a.l, b.l), er)};
+}
+__device__ __forceinline__ FF2 ff2_sub(const FF2& a, const FF2& b) {
+  const float2 sm = sub2(a.h, b.h);
+  const float2 bb = sub2(sm, a.h);
+  const float2 er = sub2(sub2(a.h, sub2(sm, bb)), __fadd2_rn(b.h, bb));
+  return FF2{sm, __fadd2_rn(sub2(a.l, b.l), er)};
+}
+__device__ __forceinline__ FF2 ff2_norm(const FF2& a) {
+  const float2 sm = __fadd2_rn(a.h, a.l);
+  return FF2{sm, sub2(a.l, sub2(sm, a.h))};
+}
+// (ch + cl) * x, normalised
+__device__ __forceinline__ FF2 ff2_mul(float2 ch, float2 cl, const FF2& x) {
+  const float2 p = __fmul2_rn(ch, x.h);
+  float2 e = __ffma2_rn(ch, x.h, neg2(p));
+  e = __ffma2_rn(ch, x.l, e);
+  e = __ffma2_rn(cl, x.h, e);
+  return ff2_norm(FF2{p, e});
+}
+__device__ __forceinline__ FF2 ld_ff2(const float4* p) {
+  const float4 v = *p;
+  return FF2{f2(v.x, v.y), f2(v.z, v.w)};
+}
+__device__ __forceinline__ void st_ff2(float4* p, const FF2& a) {
+  *p = make_float4(a.h.x, a.h.y, a.l.x, a.l.y);
+}
+
+struct StencilFF2 {
+  float c[3][2][13];  // [M, A, S][hi, lo][offset k = 0..2P], central rows
+  int lo, hi;
+};
+
+template <int P>
+struct FF2Tile {
+  static constexpr int W = 2 * P + 1;
+  static constexpr int TC = 32;
+  static constexpr int TR = P <= 4 ? 24 : 20;
+  static constexpr int HR = TR + 2 * P;           // <= 32
+  static constexpr int HC = TC + 2 * P;
+  static constexpr int HCP = HC | 1;              // input row stride in float4 slots (odd)
+  static constexpr int TCP = TC + 1;              // intermediate row stride (odd)
+  static constexpr int NC = 4;                    // columns per lane in the x_2 pass
+  static constexpr int RS = TR / 4;               // rows per lane in the x_1 pass
+  // input tile | intermediates | band rows of the tile's columns (boundary tiles); the band rows
+  // of the tile's rows reuse the input tile's space in the x_1 pass
+  static constexpr size_t off_mid = sizeof(float4) * HR * HCP;
+  static constexpr size_t off_col = off_mid + sizeof(float4) * 3 * HR * TCP;
+  static constexpr size_t smem = off_col + sizeof(float2) * 3 * W * TC;
+  static_assert(sizeof(float2) * 3 * W * TR <= off_mid, "row coefficients fit the input tile");
+};
+
+// y (or the residual, or the fused Chebyshev step) at one grid point from its double-FP32 pair
+__device__ __forceinline__ void ff2_emit(const FF2& yy, long long o1, long long o2, int mode,
+                                         const double* __restrict__ w, double* __restrict__ y,
+                                         const double* __restrict__ rhs, const Epi<double>& epi,
+                                         double ec1, double ec2, const double* dotp, double& acc) {
+  const FF2 yn = ff2_norm(yy);
+  if (mode == 2) {
+    // fused Chebyshev step: r = rhs - A w in double-FP32, the correction d = c2 D^{-1} r
+    // (+ c1 d_prev) in FP32 (a smoother step needs no more), x = x_prev + d with one FP64 add
+    const float2 q1 = ff_split_bits(rhs[o1]), q2 = ff_split_bits(rhs[o2]);
+    const FF2 rn = ff2_norm(ff2_sub(FF2{f2(q1.x, q2.x), f2(q1.y, q2.y)}, yn));
+    const float c2 = (float)ec2, c1 = (float)ec1;
+    float d1 = c2 * ff_split_bits(epi.dinv[o1]).x * rn.h.x;
+    float d2 = c2 * ff_split_bits(epi.dinv[o2]).x * rn.h.y;
+    if (epi.step > 0) {
+      d1 = fmaf(c1, ff_split_bits(epi.dprev[o1]).x, d1);
+      d2 = fmaf(c1, ff_split_bits(epi.dprev[o2]).x, d2);
+    }
+    const double e1 = f2d_bits(d1), e2 = f2d_bits(d2);
+    epi.xout[o1] = __dadd_rn(epi.xprev[o1], e1);
+    epi.xout[o2] = __dadd_rn(epi.xprev[o2], e2);
+    if (epi.dout) {
+      epi.dout[o1] = e1;
+      epi.dout[o2] = e2;
+    }
+    if (epi.rout) {
+      epi.rout[o1] = __dadd_rn(f2d_bits(rn.h.x), f2d_bits(rn.l.x));
+      epi.rout[o2] = __dadd_rn(f2d_bits(rn.h.y), f2d_bits(rn.l.y));
+    }
+    return;
+  }
+  double y1 = __dadd_rn(f2d_bits(yn.h.x), f2d_bits(yn.l.x));
+  double y2 = __dadd_rn(f2d_bits(yn.h.y), f2d_bits(yn.l.y));
+  if (mode == 1) {
+    y1 = rhs[o1] - y1;
+    y2 = rhs[o2] - y2;
+    if (dotp) acc += y1 * y1 + y2 * y2;
+  } else if (dotp) {
+    acc += w[o1] * y1 + w[o2] * y2;
+  }
+  y[o1] = y1;
+  y[o2] = y2;
+}
+
+template <int P>
+__global__ void __launch_bounds__(128, 3) apply2d_ff2_kernel(
+    int m, const float2* __restrict__ bandF, StencilFF2 cs, const double* __restrict__ w,
+    double* __restrict__ y, const double* __restrict__ rhs, int mode,
+    const double* __restrict__ alpha, const double* __restrict__ beta,
+    const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
+    Epi<double> epi) {
+  using G = FF2Tile<P>;
+  constexpr int W = G::W, TC = G::TC, TR = G::TR, HR = G::HR, HC = G::HC, HCP = G::HCP;
+  constexpr int TCP = G::TCP, NC = G::NC, RS = G::RS;
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* sIn = reinterpret_cast<float4*>(smem_raw);                   // [HR][HCP]
+  float4* sMid = reinterpret_cast<float4*>(smem_raw + G::off_mid);     // [3][HR][TCP]
+  float2* sCol = reinterpret_cast<float2*>(smem_raw + G::off_col);     // [3][W][TC]
+  float2* sRow = reinterpret_cast<float2*>(smem_raw);                  // [3][W][TR] (x_1 pass)
+  const long long N = 2LL * m * m;
+  const double* wb = w + (long long)b * N;
+  const int c0 = blockIdx.x * TC, r0 = blockIdx.y * TR;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool bcol = c0 < cs.lo || c0 + TC > cs.hi;  // tile holds non-Toeplitz columns
+  const bool brow = r0 < cs.lo || r0 + TR > cs.hi;  // ... or rows
+  {  // every load of the tile in flight before the first split (one memory latency per tile)
+    constexpr int NE = (HR * HC + 127) / 128;
+    double v1[NE], v2[NE];
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+      const int idx = threadIdx.x + 128 * t;
+      const int rr = idx / HC, cc = idx - rr * HC;
+      const int row = r0 - P + rr, col = c0 - P + cc;
+      v1[t] = v2[t] = 0.0;
+      if (idx < HR * HC && row >= 0 && row < m && col >= 0 && col < m) {
+        const long long o = (long long)row * m + col;
+        v1[t] = wb[o];
+        v2[t] = wb[(long long)m * m + o];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+      const int idx = threadIdx.x + 128 * t;
+      const int rr = idx / HC, cc = idx - rr * HC;
+      const float2 a = ff_split_bits(v1[t]), c = ff_split_bits(v2[t]);
+      if (idx < HR * HC) sIn[rr * HCP + cc] = make_float4(a.x, c.x, a.y, c.y);
+    }
+  }
+  if (bcol) {
+    constexpr int NK = (3 * W * TC + 127) / 128;
+    float2 v[NK];
+#pragma unroll
+    for (int t = 0; t < NK; ++t) {
+      const int idx = threadIdx.x + 128 * t;
+      const int xk = idx / TC, cc = idx - xk * TC;
+      v[t] = idx < 3 * W * TC && c0 + cc < m ? bandF[(size_t)xk * m + c0 + cc] : f2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < NK; ++t)
+      if (threadIdx.x + 128 * t < 3 * W * TC) sCol[threadIdx.x + 128 * t] = v[t];
+  }
+  // per-solve scalars as (hi, lo) pairs, split once per CTA (FP64 work stays off the threads)
+  __shared__ float2 s_par[3];
+  if (threadIdx.x == 0) {
+    s_par[0] = ff_split(alpha[b]);
+    s_par[1] = ff_split(beta[b]);
+    s_par[2] = ff_split((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
+  }
+  __syncthreads();
+  const float2 al = s_par[0], be = s_par[1], ga = s_par[2];
+  const float2 pmh = f2(al.x, be.x), pml = f2(al.y, be.y);  // PM = (alpha, beta) * S2 w
+  const float2 psh = f2(be.x, al.x), psl = f2(be.y, al.y);  // PS = (beta, alpha) * M2 w
+  const float2 gah = f2(ga.x, ga.x), gal = f2(ga.y, ga.y);  // PA = gamma * swap(A2 w)
+  // ---- axis x_2: lane = halo row q, NC consecutive columns per step
+  if (lane < HR) {
+    const int q = lane;
+    const int row = r0 - P + q;
+    const bool rowok = row >= 0 && row < m;
+    for (int g = warp; g < TC / NC; g += 4) {
+      const int j0 = c0 + g * NC;
+      if (rowok && j0 < m && j0 >= cs.lo && j0 + NC - 1 < cs.hi) {
+        FF2 x[NC + 2 * P];
+#pragma unroll
+        for (int t = 0; t < NC + 2 * P; ++t) x[t] = ld_ff2(&sIn[q * HCP + g * NC + t]);
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+          FF2 tM{f2(0.f, 0.f), f2(0.f, 0.f)}, tS = tM, tA = tM;
+          const FF2& xc = x[u + P];
+          ff2_fma(tM, f2(cs.c[0][0][P], cs.c[0][0][P]), f2(cs.c[0][1][P], cs.c[0][1][P]), xc);
+          ff2_fma(tS, f2(cs.c[2][0][P], cs.c[2][0][P]), f2(cs.c[2][1][P], cs.c[2][1][P]), xc);
+#pragma unroll
+          for (int t = 1; t <= P; ++t) {
+            const FF2 sp = ff2_add(x[u + P - t], x[u + P + t]);
+            const FF2 dp = ff2_sub(x[u + P + t], x[u + P - t]);
+            const int k = P + t;
+            ff2_fma(tM, f2(cs.c[0][0][k], cs.c[0][0][k]), f2(cs.c[0][1][k], cs.c[0][1][k]), sp);
+            ff2_fma(tS, f2(cs.c[2][0][k], cs.c[2][0][k]), f2(cs.c[2][1][k], cs.c[2][1][k]), sp);
+            ff2_fma(tA, f2(cs.c[1][0][k], cs.c[1][0][k]), f2(cs.c[1][1][k], cs.c[1][1][k]), dp);
+          }
+          const int cc = g * NC + u;
+          tS = ff2_norm(tS);
+          tM = ff2_norm(tM);
+          tA = ff2_norm(tA);
+          st_ff2(&sMid[(0 * HR + q) * TCP + cc], ff2_mul(pmh, pml, tS));
+          st_ff2(&sMid[(1 * HR + q) * TCP + cc], ff2_mul(psh, psl, tM));
+          st_ff2(&sMid[(2 * HR + q) * TCP + cc],
+                 ff2_mul(gah, gal, FF2{f2(tA.h.y, tA.h.x), f2(tA.l.y, tA.l.x)}));
+        }
+      } else {  // boundary columns (band rows staged in shared memory) or outside the domain
+#pragma unroll 1
+        for (int u = 0; u < NC; ++u) {
+          const int cc = g * NC + u;
+          FF2 tM{f2(0.f, 0.f), f2(0.f, 0.f)}, tS = tM, tA = tM;
+          if (rowok && c0 + cc < m) {
+#pragma unroll 1
+            for (int k = 0; k < W; ++k) {
+              const FF2 xv = ld_ff2(&sIn[q * HCP + cc + k]);
+              const float2 cM = sCol[(0 * W + k) * TC + cc], cA = sCol[(1 * W + k) * TC + cc],
+                           cS = sCol[(2 * W + k) * TC + cc];
+              ff2_fma(tM, f2(cM.x, cM.x), f2(cM.y, cM.y), xv);
+              ff2_fma(tA, f2(cA.x, cA.x), f2(cA.y, cA.y), xv);
+              ff2_fma(tS, f2(cS.x, cS.x), f2(cS.y, cS.y), xv);
+            }
+          }
+          tS = ff2_norm(tS);
+          tM = ff2_norm(tM);
+          tA = ff2_norm(tA);
+          st_ff2(&sMid[(0 * HR + q) * TCP + cc], ff2_mul(pmh, pml, tS));
+          st_ff2(&sMid[(1 * HR + q) * TCP + cc], ff2_mul(psh, psl, tM));
+          st_ff2(&sMid[(2 * HR + q) * TCP + cc],
+                 ff2_mul(gah, gal, FF2{f2(tA.h.y, tA.h.x), f2(tA.l.y, tA.l.x)}));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (brow) {  // band rows of the tile's rows, into the input tile's space
+    constexpr int NK = (3 * W * TR + 127) / 128;
+    float2 v[NK];
+#pragma unroll
+    for (int t = 0; t < NK; ++t) {
+      const int idx = threadIdx.x + 128 * t;
+      const int xk = idx / TR, rr = idx - xk * TR;
+      v[t] = idx < 3 * W * TR && r0 + rr < m ? bandF[(size_t)xk * m + r0 + rr] : f2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < NK; ++t)
+      if (threadIdx.x + 128 * t < 3 * W * TR) sRow[threadIdx.x + 128 * t] = v[t];
+    __syncthreads();
+  }
+  // ---- axis x_1: lane = column, RS rows per warp: y = M1 PM + S1 PS + A1 PA
+  double acc = 0.0, ec1 = 0.0, ec2 = 0.0;
+  if (mode == 2) cheb_coef_cta(epi.lmax[b], epi.step, ec1, ec2);
+  const int cc = lane, j = c0 + cc;
+  const int rb = warp * RS;
+  if (j < m) {
+    if (r0 + rb >= cs.lo && r0 + rb + RS - 1 < cs.hi) {
+      FF2 yy[RS];
+#pragma unroll
+      for (int r = 0; r < RS; ++r) yy[r] = FF2{f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll 1
+      for (int band = 0; band < 2; ++band) {  // M on PM, S on PS (symmetric)
+        const int x = band == 0 ? 0 : 2;
+        FF2 v[RS + 2 * P];
+#pragma unroll
+        for (int t = 0; t < RS + 2 * P; ++t) v[t] = ld_ff2(&sMid[(band * HR + rb + t) * TCP + cc]);
+        float ch[P + 1], cl[P + 1];
+#pragma unroll
+        for (int t = 0; t <= P; ++t) {
+          ch[t] = x == 0 ? cs.c[0][0][P + t] : cs.c[2][0][P + t];
+          cl[t] = x == 0 ? cs.c[0][1][P + t] : cs.c[2][1][P + t];
+        }
+#pragma unroll
+        for (int r = 0; r < RS; ++r) {
+          ff2_fma(yy[r], f2(ch[0], ch[0]), f2(cl[0], cl[0]), v[r + P]);
+#pragma unroll
+          for (int t = 1; t <= P; ++t)
+            ff2_fma(yy[r], f2(ch[t], ch[t]), f2(cl[t], cl[t]), ff2_add(v[r + P - t], v[r + P + t]));
+        }
+      }
+      {  // A on PA (skew)
+        FF2 v[RS + 2 * P];
+#pragma unroll
+        for (int t = 0; t < RS + 2 * P; ++t) v[t] = ld_ff2(&sMid[(2 * HR + rb + t) * TCP + cc]);
+#pragma unroll
+        for (int r = 0; r < RS; ++r)
+#pragma unroll
+          for (int t = 1; t <= P; ++t)
+            ff2_fma(yy[r], f2(cs.c[1][0][P + t], cs.c[1][0][P + t]),
+                    f2(cs.c[1][1][P + t], cs.c[1][1][P + t]), ff2_sub(v[r + P + t], v[r + P - t]));
+      }
+#pragma unroll
+      for (int r = 0; r < RS; ++r) {
+        const long long o1 = (long long)b * N + (long long)(r0 + rb + r) * m + j;
+        ff2_emit(yy[r], o1, o1 + (long long)m * m, mode, w, y, rhs, epi, ec1, ec2, dotp, acc);
+      }
+    } else {  // boundary rows (band rows staged in shared memory)
+#pragma unroll 1
+      for (int r = 0; r < RS; ++r) {
+        const int i = r0 + rb + r;
+        if (i >= m) break;
+        FF2 yy{f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll 1
+        for (int band = 0; band < 3; ++band) {
+          const int x = band == 0 ? 0 : band == 1 ? 2 : 1;
+#pragma unroll 1
+          for (int k = 0; k < W; ++k) {
+            const float2 cX = sRow[(x * W + k) * TR + rb + r];
+            ff2_fma(yy, f2(cX.x, cX.x), f2(cX.y, cX.y), ld_ff2(&sMid[(band * HR + rb + r + k) * TCP + cc]));
+          }
+        }
+        const long long o1 = (long long)b * N + (long long)i * m + j;
+        ff2_emit(yy, o1, o1 + (long long)m * m, mode, w, y, rhs, epi, ec1, ec2, dotp, acc);
+      }
+    }
+  }
+  if (dotp) {
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0)
+      dotp[(size_t)b * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = sum;
+  }
+}
+
+template <int P>
+static void set_ff2_attr() {
+  cudaFuncSetAttribute(apply2d_ff2_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)FF2Tile<P>::smem);
+}
+
+// Central rows split into (hi, lo); false unless M and S are palindromes and A is skew with a
+// zero centre (the folded interior form needs that exactly).
+static bool stencil_ff2(const StencilHost& sh, StencilFF2& cs) {
+  const int P = sh.P;
+  if (!stencil_folds(sh)) return false;
+  for (int x = 0; x < 3; ++x)
+    for (int k = 0; k < 13; ++k) {
+      const double v = k < 2 * P + 1 ? sh.c[x][k] : 0.0;
+      const float h = (float)v;
+      cs.c[x][0][k] = h;
+      cs.c[x][1][k] = (float)(v - (double)h);
+    }
+  cs.lo = sh.lo;
+  cs.hi = sh.hi;
+  return true;
+}
+
+template <int P>
+static bool launch_ff2_P(int m, const StencilHost& sh, const double* w, double* y,
+                         const double* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                         const int* active, cudaStream_t s) {
+  using G = FF2Tile<P>;
+  StencilFF2 cs;
+  if (!stencil_ff2(sh, cs)) return false;
+  dim3 grid((m + G::TC - 1) / G::TC, (m + G::TR - 1) / G::TR, B);
+  if (dotp && (long long)grid.x * grid.y > kMaxPartials) return false;
+  apply2d_ff2_kernel<P><<<grid, 128, G::smem, s>>>(m, sh.ffT, cs, w, y, rhs, mode, c.alpha, c.beta,
+                                                   c.gsc, active, dotp, g_epi<double>);
+  count_launch();
+  if (nblk) *nblk = grid.x * grid.y;
+  return true;
+}
+
 static thread_local int g_ff_inner = 0;  // the calling thread's FP64 applies run in double-FP32
 void set_fp64_emulated(int on) { g_ff_inner = on; }
 int fp64_emulated() { return g_ff_inner || g_ff_forced; }
@@ -1454,6 +2143,19 @@ static bool try_apply2d_ff(int m, int P, const double* bands, const double* w, d
   if (mode == 2 && !g_epi<double>.dinv) return false;
   StencilHost sh;
   if (!find_level(bands, sh) || sh.P != P || !sh.ffT) return false;
+  if (g_ff_kernel == 2) {
+    bool ok = false;
+    switch (P) {
+      case 1: ok = launch_ff2_P<1>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
+      case 2: ok = launch_ff2_P<2>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
+      case 3: ok = launch_ff2_P<3>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
+      case 4: ok = launch_ff2_P<4>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
+      case 5: ok = launch_ff2_P<5>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
+      case 6: ok = launch_ff2_P<6>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
+      default: break;
+    }
+    if (ok) return true;
+  }
   if (dotp && (long long)((m + 63) / 64) * ((m + 15) / 16) > kMaxPartials) return false;
   switch (P) {
     case 1: return launch_ff_P<1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
@@ -1479,6 +2181,10 @@ int prepare_kernels() {
   set_v2_attrs<double, 4>(); set_v2_attrs<double, 5>(); set_v2_attrs<double, 6>();
   set_ff_attr<1, 16>(); set_ff_attr<2, 16>(); set_ff_attr<3, 16>();
   set_ff_attr<4, 16>(); set_ff_attr<5, 16>(); set_ff_attr<6, 16>();
+  set_v5_attr<1>(); set_v5_attr<2>(); set_v5_attr<3>();
+  set_v5_attr<4>(); set_v5_attr<5>(); set_v5_attr<6>();
+  set_ff2_attr<1>(); set_ff2_attr<2>(); set_ff2_attr<3>();
+  set_ff2_attr<4>(); set_ff2_attr<5>(); set_ff2_attr<6>();
   cudaError_t e1 = cudaFuncSetAttribute(apply2d_kernel<double>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmemCap);
   cudaError_t e2 = cudaFuncSetAttribute(apply2d_kernel<float>,
@@ -1523,6 +2229,10 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
         try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, 8))
       return 0;
     int tuned = g_use_v2 == 2 ? tuned_variant(sizeof(T), m, P, B) : 0;
+    if constexpr (sizeof(T) == 4) {
+      if (tuned == 5 && try_apply2d_v5(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+        return 0;
+    }
     if (tuned == 1 && try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, 16))
       return 0;
     if (tuned == 2 && try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, 8))
@@ -1530,8 +2240,13 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
     if (tuned == 3 && try_apply2d_v2<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
       return 0;
     if (tuned == 4 && mode != 2) goto plain_v1;
-    // FP32: v3 (packed pairs) first; FP64: v2 first (v3's FP64 instantiation is register-bound)
-    if (g_use_v2 == 2 && sizeof(T) == 4 &&
+    // FP32: v5, then v3 (packed pairs); FP64: v2 first (v3's FP64 instantiation is register-bound)
+    if constexpr (sizeof(T) == 4) {
+      if (g_use_v2 == 2 && tuned == 0 &&
+          try_apply2d_v5(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+        return 0;
+    }
+    if (g_use_v2 >= 2 && sizeof(T) == 4 &&
         try_apply2d_v3<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
       return 0;
     if (g_use_v2 >= 1 && try_apply2d_v2<T>(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
@@ -1638,7 +2353,7 @@ int tune_apply2d(int m, int P, const T* bands, const T* w, T* y, int B, Coef c, 
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return 0;
   float best = 1e30f;
   int bestv = 0;
-  for (int v = 1; v <= 2; ++v) {
+  for (int v : {5, 1, 2}) {
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tuned[key] = v;

@@ -6,6 +6,7 @@
 
 #include "krylov.h"
 #include "mg.h"
+#include "ffmath.h"
 
 namespace cd {
 
@@ -16,49 +17,67 @@ MgData::~MgData() {
 }
 
 // ------------------------------------------------------------------ transfer kernels
-// coarse(J) = sum over taps a in {0,1,2}^d of prod_l w_{a_l} fine(2 J_l + a_l), w = (1/2, 1, 1/2)
+// coarse(J) = sum over taps a in {0,1,2}^d of prod_l w_{a_l} fine(2 J_l + a_l), w = (1/2, 1, 1/2).
+// The tap weights (1, 1/2, 1/4, 1/8) are exact in every precision; the index arithmetic is 32-bit
+// (one solve's vector has fewer than 2^31 entries on every level this library builds: the
+// set-up rejects larger problems).
 template <typename T>
 __global__ void __launch_bounds__(256) restrict_kernel(int d, int mf, int mc, const T* __restrict__ fine,
                                                        T* __restrict__ coarse,
                                                        const int* __restrict__ active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  long long nfc = 1, ncc = 1;
-  for (int l = 0; l < d; ++l) {
-    nfc *= mf;
-    ncc *= mc;
-  }
-  const long long total = (long long)d * ncc;
+  const int nfc = d == 2 ? mf * mf : mf * mf * mf, ncc = d == 2 ? mc * mc : mc * mc * mc;
+  const int total = d * ncc;
   const T* fb = fine + (long long)b * d * nfc;
   T* cb = coarse + (long long)b * total;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int comp = (int)(idx / ncc);
-    long long rem = idx - comp * ncc;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int comp = idx / ncc;
+    int rem = idx - comp * ncc;
     int J[3] = {0, 0, 0};
     for (int l = d - 1; l >= 0; --l) {
-      J[l] = (int)(rem % mc);
-      rem /= mc;
+      const int q = rem / mc;
+      J[l] = rem - q * mc;
+      rem = q;
     }
+    const T* src = fb + (long long)comp * nfc;
     T acc = 0;
-    const int ntap = d == 2 ? 9 : 27;
-    for (int t = 0; t < ntap; ++t) {
-      int tt = t;
-      long long off = 0;
-      T w = 1;
-      bool ok = true;
-      for (int l = 0; l < d; ++l) {
-        const int a = tt % 3;
-        tt /= 3;
-        const int i = 2 * J[l] + a;
-        if (i >= mf) {
-          ok = false;
-          break;
+    if (d == 2) {
+#pragma unroll
+      for (int a0 = 0; a0 < 3; ++a0) {
+        const int i0 = 2 * J[0] + a0;
+        if (i0 >= mf) break;
+        T row = 0;
+#pragma unroll
+        for (int a1 = 0; a1 < 3; ++a1) {
+          const int i1 = 2 * J[1] + a1;
+          if (i1 >= mf) break;
+          const T v = src[i0 * mf + i1];
+          row += a1 == 1 ? v : T(0.5) * v;
         }
-        w *= (a == 1) ? T(1) : T(0.5);
-        off = off * mf + i;
+        acc += a0 == 1 ? row : T(0.5) * row;
       }
-      if (ok) acc += w * fb[comp * nfc + off];
+    } else {
+#pragma unroll 1
+      for (int a0 = 0; a0 < 3; ++a0) {
+        const int i0 = 2 * J[0] + a0;
+        if (i0 >= mf) break;
+        T pl = 0;
+        for (int a1 = 0; a1 < 3; ++a1) {
+          const int i1 = 2 * J[1] + a1;
+          if (i1 >= mf) break;
+          T row = 0;
+#pragma unroll
+          for (int a2 = 0; a2 < 3; ++a2) {
+            const int i2 = 2 * J[2] + a2;
+            if (i2 >= mf) break;
+            const T v = src[((long long)i0 * mf + i1) * mf + i2];
+            row += a2 == 1 ? v : T(0.5) * v;
+          }
+          pl += a1 == 1 ? row : T(0.5) * row;
+        }
+        acc += a0 == 1 ? pl : T(0.5) * pl;
+      }
     }
     cb[idx] = acc;
   }
@@ -71,59 +90,71 @@ __global__ void __launch_bounds__(256) prolong_kernel(int d, int mf, int mc, con
                                                       const int* __restrict__ active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  long long nfc = 1, ncc = 1;
-  for (int l = 0; l < d; ++l) {
-    nfc *= mf;
-    ncc *= mc;
-  }
-  const long long total = (long long)d * nfc;
+  const int nfc = d == 2 ? mf * mf : mf * mf * mf, ncc = d == 2 ? mc * mc : mc * mc * mc;
+  const int total = d * nfc;
   const T* cb = coarse + (long long)b * d * ncc;
   T* fb = fine + (long long)b * total;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int comp = (int)(idx / nfc);
-    long long rem = idx - comp * nfc;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int comp = idx / nfc;
+    int rem = idx - comp * nfc;
     int I[3] = {0, 0, 0};
     for (int l = d - 1; l >= 0; --l) {
-      I[l] = (int)(rem % mf);
-      rem /= mf;
+      const int q = rem / mf;
+      I[l] = rem - q * mf;
+      rem = q;
     }
-    // per axis: up to two coarse indices with weights
-    int js[3][2];
-    T ws[3][2];
-    int nj[3];
+    // per axis: one coarse index with weight 1 (odd i) or up to two with weight 1/2 (even i)
+    int j0[3], j1[3];  // j1 = -1: no second index
+    bool half[3];
     for (int l = 0; l < d; ++l) {
       const int i = I[l];
-      nj[l] = 0;
       if (i & 1) {
-        const int j = (i - 1) / 2;
-        if (j < mc) {
-          js[l][nj[l]] = j;
-          ws[l][nj[l]++] = T(1);
-        }
+        j0[l] = (i - 1) / 2;
+        j1[l] = -1;
+        half[l] = false;
       } else {
-        const int j0 = i / 2, j1 = i / 2 - 1;
-        if (j0 < mc) {
-          js[l][nj[l]] = j0;
-          ws[l][nj[l]++] = T(0.5);
-        }
-        if (j1 >= 0 && j1 < mc) {
-          js[l][nj[l]] = j1;
-          ws[l][nj[l]++] = T(0.5);
-        }
+        j0[l] = i / 2 < mc ? i / 2 : -1;
+        j1[l] = i / 2 - 1;
+        half[l] = true;
       }
     }
+    const T* src = cb + (long long)comp * ncc;
     T acc = 0;
     if (d == 2) {
-      for (int a = 0; a < nj[0]; ++a)
-        for (int c = 0; c < nj[1]; ++c)
-          acc += ws[0][a] * ws[1][c] * cb[comp * ncc + (long long)js[0][a] * mc + js[1][c]];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int ja = a == 0 ? j0[0] : j1[0];
+        if (ja < 0 || ja >= mc) continue;
+        T row = 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int jc = c == 0 ? j0[1] : j1[1];
+          if (jc < 0 || jc >= mc) continue;
+          row += src[ja * mc + jc];
+        }
+        acc += half[1] ? T(0.5) * row : row;
+      }
+      if (half[0]) acc = T(0.5) * acc;
     } else {
-      for (int a = 0; a < nj[0]; ++a)
-        for (int c = 0; c < nj[1]; ++c)
-          for (int e = 0; e < nj[2]; ++e)
-            acc += ws[0][a] * ws[1][c] * ws[2][e] *
-                   cb[comp * ncc + ((long long)js[0][a] * mc + js[1][c]) * mc + js[2][e]];
+      for (int a = 0; a < 2; ++a) {
+        const int ja = a == 0 ? j0[0] : j1[0];
+        if (ja < 0 || ja >= mc) continue;
+        T pl = 0;
+        for (int c = 0; c < 2; ++c) {
+          const int jc = c == 0 ? j0[1] : j1[1];
+          if (jc < 0 || jc >= mc) continue;
+          T row = 0;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int je = e == 0 ? j0[2] : j1[2];
+            if (je < 0 || je >= mc) continue;
+            row += src[((long long)ja * mc + jc) * mc + je];
+          }
+          pl += half[2] ? T(0.5) * row : row;
+        }
+        acc += half[1] ? T(0.5) * pl : pl;
+      }
+      if (half[0]) acc = T(0.5) * acc;
     }
     fb[idx] += acc;
   }
@@ -191,19 +222,41 @@ __device__ __forceinline__ void cheb_params(double lmax, double& theta, double& 
   delta = 0.5 * (hi - lo);
 }
 
-// d = D^{-1} r / theta; x = (xzero ? 0 : x) + d   (dinv: precomputed 1 / diag per solve)
+// d = D^{-1} r / theta; x = (xzero ? 0 : x) + d   (dinv: precomputed 1 / diag per solve).
+// The per-solve scalar is formed once per CTA (FP64 divisions per thread are expensive on
+// GB300).  lowp (FP64 vectors only): d in FP32 arithmetic from the FP32 truncations of dinv and
+// r, exactly widened (a smoother step needs no more; x and the residuals stay FP64).
 template <typename T>
 __global__ void __launch_bounds__(256) cheb_first_kernel(long long N, const T* __restrict__ dinv,
                                                          const double* __restrict__ lmax,
                                                          const T* __restrict__ r, T* __restrict__ x,
                                                          T* __restrict__ dv, int xzero,
-                                                         const int* __restrict__ active) {
+                                                         const int* __restrict__ active, int lowp) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  double th, de;
-  cheb_params(lmax[b], th, de);
-  const T ith = T(1.0 / th);
+  __shared__ double s_ith;
+  __shared__ float s_ithf;
+  if (threadIdx.x == 0) {
+    double th, de;
+    cheb_params(lmax[b], th, de);
+    s_ith = 1.0 / th;
+    s_ithf = (float)s_ith;
+  }
+  __syncthreads();
   const long long base = (long long)b * N;
+  if (sizeof(T) == 8 && lowp) {
+    const float ith = s_ithf;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+      const float vf = ff_split_bits((double)dinv[base + idx]).x *
+                       ff_split_bits((double)r[base + idx]).x * ith;
+      const T v = (T)f2d_bits(vf);
+      dv[base + idx] = v;
+      x[base + idx] = xzero ? v : x[base + idx] + v;
+    }
+    return;
+  }
+  const T ith = T(s_ith);
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
        idx += (long long)gridDim.x * blockDim.x) {
     const T v = dinv[base + idx] * r[base + idx] * ith;
@@ -221,15 +274,21 @@ __global__ void __launch_bounds__(256) cheb_next_kernel(long long N, const T* __
                                                         const int* __restrict__ active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  double th, de;
-  cheb_params(lmax[b], th, de);
-  const double sigma = th / de;
-  double rho_prev = 1.0 / sigma, rho = rho_prev;
-  for (int j = 1; j <= k; ++j) {
-    rho_prev = rho;
-    rho = 1.0 / (2.0 * sigma - rho_prev);
+  __shared__ double s_c[2];
+  if (threadIdx.x == 0) {
+    double th, de;
+    cheb_params(lmax[b], th, de);
+    const double sigma = th / de;
+    double rho_prev = 1.0 / sigma, rho = rho_prev;
+    for (int j = 1; j <= k; ++j) {
+      rho_prev = rho;
+      rho = 1.0 / (2.0 * sigma - rho_prev);
+    }
+    s_c[0] = rho * rho_prev;
+    s_c[1] = 2.0 * rho / de;
   }
-  const T c1 = T(rho * rho_prev), c2 = T(2.0 * rho / de);
+  __syncthreads();
+  const T c1 = T(s_c[0]), c2 = T(s_c[1]);
   const long long base = (long long)b * N;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -302,16 +361,21 @@ __global__ void scale_kernel(long long N, double* v, const double* sc) {
 
 // ------------------------------------------------------------------ coarsest solve
 template <typename T>
-__global__ void coarse_solve_kernel(int nc, const T* __restrict__ inv, const T* __restrict__ rhs,
-                                    T* __restrict__ x, const int* __restrict__ active) {
-  const int b = blockIdx.x;
+__global__ void __launch_bounds__(256) coarse_solve_kernel(int nc, const T* __restrict__ inv,
+                                                           const T* __restrict__ rhs,
+                                                           T* __restrict__ x,
+                                                           const int* __restrict__ active) {
+  // one warp per row of the dense inverse (coalesced row reads), 8 rows per CTA
+  const int b = blockIdx.y;
   if (active && !active[b]) return;
-  const T* Ab = inv + (size_t)b * nc * nc;
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    T s = 0;
-    for (int j = 0; j < nc; ++j) s += Ab[(size_t)i * nc + j] * rhs[(size_t)b * nc + j];
-    x[(size_t)b * nc + i] = s;
-  }
+  const int lane = threadIdx.x & 31, i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= nc) return;
+  const T* Ai = inv + ((size_t)b * nc + i) * nc;
+  const T* rb = rhs + (size_t)b * nc;
+  T s = 0;
+  for (int j = lane; j < nc; j += 32) s += Ai[j] * rb[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[(size_t)b * nc + i] = s;
 }
 
 // ------------------------------------------------------------------ host side
@@ -510,7 +574,8 @@ static void smooth(MgData& mg, int l, int B, const T* bl, T* xl, bool xzero, Coe
     rsrc = r;
   }
   const T* dinv = (const T*)lb.dinv;
-  cheb_first_kernel<T><<<g, 256, 0, s>>>(N, dinv, lm, rsrc, xl, dv, xzero ? 1 : 0, active);
+  cheb_first_kernel<T><<<g, 256, 0, s>>>(N, dinv, lm, rsrc, xl, dv, xzero ? 1 : 0, active,
+                                         fp64_emulated());
   count_launch();
   for (int k = 1; k < mg.deg; ++k) {
     launch_apply<T>(mg.d, m, mg.P, bands, dv, r, rsrc, 1, B, c, nullptr, nullptr, active, scr, s);
@@ -532,7 +597,7 @@ static void smooth_pre_fused(MgData& mg, int l, int B, const T* bl, T* X0, T* XB
   MgLevelBuf& lb = sizeof(T) == 8 ? mg.lv64[l] : mg.lv32[l];
   const double* lm = mg.lmax + (size_t)l * mg.B;
   cheb_first_kernel<T><<<grid_for(N, B), 256, 0, s>>>(N, (const T*)lb.dinv, lm, bl, X0, (T*)lb.dv, 1,
-                                                      active);
+                                                      active, fp64_emulated());
   count_launch();
   Epi<T> e{X0, X0, XB, nullptr, nullptr, lm, 1, (const T*)lb.dinv};
   launch_apply<T>(mg.d, m, mg.P, level_bands<T>(mg, l), X0, nullptr, bl, 2, B, c, nullptr, nullptr,
@@ -559,8 +624,8 @@ static void vcycle_rec(MgData& mg, int l, int B, const T* bl, T* xl, Coef c, con
                        T* fine_scr, cudaStream_t s, int post) {
   T* scr = l == 0 ? fine_scr : level_scratch<T>(mg);
   if (l == mg.L - 1) {
-    coarse_solve_kernel<T><<<B, 128, 0, s>>>(mg.nc, sizeof(T) == 8 ? (const T*)mg.cinv64 : (const T*)mg.cinv32,
-                                             bl, xl, active);
+    coarse_solve_kernel<T><<<dim3((mg.nc + 7) / 8, B), 256, 0, s>>>(
+        mg.nc, sizeof(T) == 8 ? (const T*)mg.cinv64 : (const T*)mg.cinv32, bl, xl, active);
     count_launch();
     return;
   }

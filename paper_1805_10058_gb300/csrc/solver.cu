@@ -167,10 +167,32 @@ static void fd_pass(cd_solver h, int axis, int B, const T* G, const T* in, T* ou
   launch_fd_axis<T>(h->d, h->m, axis, B, G, in, out, sc, active, h->s);
 }
 
+// The inner FP64 solves of a mixed-precision solve apply a fast-diagonalisation preconditioner
+// in FP32 (tensor-core transforms): a preconditioner needs no FP64 accuracy, and the FP64 FD
+// passes run on GB300's narrow FP64 pipe.  Set by the refinement loop for its FP64 group.
+static thread_local int g_lowp_prec = 0;
+
+template <typename T>
+static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* active);
+
+// z = B^{-1} r for an FD preconditioner of an FP64 solve, computed in FP32
+static void apply_fd_lowp(cd_solver h, int pc, int B, const double* r, double* z, const int* active) {
+  Workspace& w = ws_of<float>(h);
+  to_f32(h->N, B, r, w.r.as<float>(), active, h->s);
+  apply_prec<float>(h, pc, B, w.r.as<float>(), w.z.as<float>(), active);
+  to_f64(h->N, B, w.z.as<float>(), z, active, h->s);
+}
+
 // z = B^{-1} r for the preconditioner kind pc.
 template <typename T>
 static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* active) {
   Workspace& w = ws_of<T>(h);
+  if constexpr (sizeof(T) == 8) {
+    if (g_lowp_prec && (pc == CD_PC_FD_D || pc == CD_PC_FD_T)) {
+      apply_fd_lowp(h, pc, B, r, z, active);
+      return;
+    }
+  }
   if (pc == CD_PC_NONE) {
     vcopy<T>(h->N, B, r, z, active, h->s);
     return;
@@ -268,11 +290,12 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
   const int nb = partial_blocks(N);
   // a Krylov-smoothed / multigrid or tensor-core (TF32) preconditioner is not an exactly
   // fixed symmetric operator: use the flexible update there
-  const int flexible =
-      (pc == CD_PC_MG || pc == CD_PC_MIM || pc == CD_PC_WL ||
-       (sizeof(T) == 4 && h->opt.fd_tensor_cores && (pc == CD_PC_FD_D || pc == CD_PC_FD_T)))
-          ? 1
-          : 0;
+  const bool fd = pc == CD_PC_FD_D || pc == CD_PC_FD_T;
+  const int flexible = (pc == CD_PC_MG || pc == CD_PC_MIM || pc == CD_PC_WL ||
+                        (sizeof(T) == 4 && h->opt.fd_tensor_cores && fd) ||
+                        (sizeof(T) == 8 && g_lowp_prec && fd))
+                           ? 1
+                           : 0;
   vzero<T>(N, B, w.x.as<T>(), outer_active, h->s);
   apply_prec<T>(h, pc, B, w.r.as<T>(), w.z.as<T>(), outer_active);
   launch_dot<T>(w.r.as<T>(), w.r.as<T>(), N, B, h->part[1].as<double>(), nb, outer_active, h->s);
@@ -283,7 +306,8 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
   cudaGraphExec_t exec = nullptr;
   uint64_t nodes = 0;
   if (h->opt.use_graphs) {
-    auto key = std::make_tuple((int)(sizeof(T) == 4), B, pc, flexible, fp64_emulated(), maxit);
+    auto key = std::make_tuple((int)(sizeof(T) == 4), B, pc, flexible,
+                               fp64_emulated() + 2 * g_lowp_prec, maxit);
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
       exec = it->second.first;
@@ -512,8 +536,10 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, double* x
       const int cap = (step == 0 || ext) ? h->opt.maxit
                                          : std::min({h->opt.maxit, h->opt.inner_maxit, 500});
       set_fp64_emulated(emu_inner ? 1 : 0);
+      g_lowp_prec = h->opt.precision == CD_PREC_FP32_IR ? 1 : 0;
       cd_status st = run_pcg<double>(h, B, pc, tol2v, cap, m[g]);
       set_fp64_emulated(0);
+      g_lowp_prec = 0;
       if (st != CD_OK) return st;
       add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), m[g],
                                                           h->ir_inner_total.as<int>());
@@ -713,6 +739,10 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     set_error("alpha and beta must be finite and > 0");
     return CD_EINVAL;
   }
+  if (cd_dofs(d, p, n) >= (size_t(1) << 31)) {  // the kernels index one solve's vector in 32 bits
+    set_error("d (n+p-2)^d must be below 2^31");
+    return CD_EINVAL;
+  }
   std::unique_ptr<cd_solver_s> h(new cd_solver_s());
   h->d = d;
   h->p = p;
@@ -843,10 +873,10 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   {
     const char* v = std::getenv("CURLDIV_APPLY_KERNEL");
     const std::string vs = v ? v : "";
-    set_apply_variant(vs == "v1" ? 0 : vs == "v2" ? 1 : 2);
+    set_apply_variant(vs == "v1" ? 0 : vs == "v2" ? 1 : vs == "v3" ? 3 : 2);
     const char* v64 = std::getenv("CURLDIV_APPLY_KERNEL_FP64");
     const std::string v64s = v64 ? v64 : "";
-    set_apply_fp64_variant(v64s == "v3" ? 1 : v64s == "ff" ? 2 : 0);
+    set_apply_fp64_variant(v64s == "v3" ? 1 : v64s == "ff" ? 2 : v64s == "ff2" ? 3 : v64s == "ff1" ? 4 : 0);
     const char* v3d = std::getenv("CURLDIV_APPLY3D_KERNEL");
     set_apply3d_variant(v3d && std::string(v3d) == "multipass" ? 0 : 1);
   }

@@ -17,10 +17,13 @@ from paper_1805_10058_gb300 import inputs  # noqa: E402
 FF_TOL = 5e-13
 
 
+@pytest.mark.parametrize("kernel", ["ff1", "ff2"])
 @pytest.mark.parametrize("p,n,beta", [(1, 9, 1.0), (2, 40, 1e-6), (3, 70, 1e3), (4, 33, 0.01),
-                                      (6, 30, 1e6), (3, 256, 1e-3)])
-def test_double_fp32_apply_matches_oracle(p, n, beta, monkeypatch):
-    monkeypatch.setenv("CURLDIV_APPLY_KERNEL_FP64", "ff")
+                                      (5, 41, 1e-6), (6, 30, 1e6), (3, 256, 1e-3)])
+def test_double_fp32_apply_matches_oracle(p, n, beta, kernel, monkeypatch):
+    """Both double-FP32 kernels: ff1 (plain band sums) and ff2 (packed pairs, folded interior
+    stencils); sizes span several tiles with ragged tails in both axes."""
+    monkeypatch.setenv("CURLDIV_APPLY_KERNEL_FP64", kernel)
     d, B = 2, 3
     W = inputs.uniform_rhs(d, p, n, seed=31, nrhs=B)
     s = cdl.Solver(d, p, n, 1.0, beta, max_batch=B, autotune=0)
@@ -34,7 +37,7 @@ def test_double_fp32_apply_matches_oracle(p, n, beta, monkeypatch):
         bound = abs_matvec_bound(A, W[k])
         err = np.abs(Y[k] - A @ W[k]) / bound
         worst = max(worst, float(err.max()))
-    print("double-FP32 apply, worst error / (|A||w|):", p, n, beta, worst)
+    print("double-FP32 apply", kernel, "worst error / (|A||w|):", p, n, beta, worst)
     assert worst <= FF_TOL, worst
 
 

@@ -35,12 +35,12 @@ APPLY_CASES = [(2, 1, 9), (2, 2, 16), (2, 3, 37), (2, 5, 30), (2, 2, 3), (2, 6, 
                (3, 1, 5), (3, 2, 7), (3, 3, 9), (3, 4, 6)]
 
 
-@pytest.mark.parametrize("variant", ["v3", "v2", "v1"])
+@pytest.mark.parametrize("variant", ["v5", "v3", "v2", "v1"])
 @pytest.mark.parametrize("d,p,n", APPLY_CASES)
 def test_apply_fp64_and_fp32_match_oracle(d, p, n, variant, monkeypatch):
-    """Every 2D kernel (v3 default, v2, plain shared-memory v1) and both 3D kernels (streaming
-    default, three banded passes) against the oracle."""
-    if d == 3 and variant == "v1":
+    """Every 2D kernel (FP32: v5 folded tiles, v3 packed pairs; v2; plain shared-memory v1) and
+    both 3D kernels (streaming default, three banded passes) against the oracle."""
+    if d == 3 and variant in ("v1", "v5"):
         pytest.skip("two 3D kernels")
     if d == 3:
         monkeypatch.setenv("CURLDIV_APPLY3D_KERNEL", "stream" if variant == "v3" else "multipass")
@@ -49,7 +49,7 @@ def test_apply_fp64_and_fp32_match_oracle(d, p, n, variant, monkeypatch):
         monkeypatch.setenv("CURLDIV_APPLY_KERNEL_FP64", "v3" if variant == "v3" else "v2")
     alphas = np.array([1.0, 0.5, 3.0])
     betas = np.array([0.1, 7.0, 3.0])
-    s = cdl.Solver(d, p, n, max_batch=3)
+    s = cdl.Solver(d, p, n, max_batch=3, autotune=0)
     N = s.N
     W = inputs.uniform_rhs(d, p, n, seed=11, nrhs=3)
     y = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
