@@ -7,6 +7,11 @@ inside a component the Kronecker order of the tensor-product index
 (i_1, ..., i_d), x_1 slowest and x_d fastest.  DoF count d * m^d with
 m = n + p - 2.
 
+``n`` is the number of intervals per direction, or a tuple (n_1, ..., n_d) of
+per-direction counts: the anisotropic meshes n_l = nu_l n of Section 5 (the
+spline space is then the tensor product of the 1D spaces of each direction,
+and m_l = n_l + p - 2 unknowns per direction per component).
+
 Two independent routes to the same matrix:
 
 * ``galerkin_quadrature`` evaluates curl and div of every vector basis
@@ -24,9 +29,19 @@ import scipy.sparse as sp
 from . import iga1d
 
 
+def axis_counts(d, n):
+    """Per-direction interval counts: (n,) * d for an integer n, else the given tuple."""
+    if np.isscalar(n):
+        return (int(n),) * d
+    ns = tuple(int(v) for v in n)
+    if len(ns) != d:
+        raise ValueError("one interval count per direction")
+    return ns
+
+
 def dofs(d, p, n):
-    """Matrix size d * (n+p-2)^d (Section 5.1)."""
-    return d * (n + p - 2) ** d
+    """Matrix size d * prod_l (n_l+p-2) (Section 5.1; d (n+p-2)^d on a uniform mesh)."""
+    return d * int(np.prod([v + p - 2 for v in axis_counts(d, n)]))
 
 
 def _kron_all(mats):
@@ -44,20 +59,23 @@ def _eval_ops(d, p, n, nq, rows0=None):
     quadrature weights.  ``rows0`` restricts the x_1 points to a slice (the
     operators then cover only those points, in the same order).
     """
-    x, w1 = iga1d.gauss_points(n, nq)
-    v, g = iga1d.eval_interior(p, n, x)
-    v = sp.csr_matrix(v)
-    g = sp.csr_matrix(g)
+    ns = axis_counts(d, n)
+    vs, gs, ws = [], [], []
+    for l in range(d):  # the 1D Gauss grid and basis of direction l
+        x, wl = iga1d.gauss_points(ns[l], nq)
+        v, g = iga1d.eval_interior(p, ns[l], x)
+        vs.append(sp.csr_matrix(v))
+        gs.append(sp.csr_matrix(g))
+        ws.append(wl)
     sl = slice(None) if rows0 is None else rows0
-    v0, g0, w0 = v[sl], g[sl], w1[sl]
-    first = lambda l: g0 if l == 0 else v0  # noqa: E731
-    vals = _kron_all([v0] + [v] * (d - 1))
+    vs[0], gs[0], ws[0] = vs[0][sl], gs[0][sl], ws[0][sl]
+    vals = _kron_all(vs)
     dx = []
     for l in range(d):
-        dx.append(_kron_all([first(l)] + [g if k == l else v for k in range(1, d)]))
-    w = w0
-    for _ in range(d - 1):
-        w = np.kron(w, w1)
+        dx.append(_kron_all([gs[k] if k == l else vs[k] for k in range(d)]))
+    w = ws[0]
+    for l in range(1, d):
+        w = np.kron(w, ws[l])
     return vals, dx, w
 
 
@@ -101,26 +119,40 @@ def galerkin_quadrature(d, p, n, alpha, beta, nq=None, parts=False):
 
 
 def galerkin_kron(d, p, n, alpha, beta, mats=None, parts=False):
-    """eq:matr_Amu (d=2) / eq:matr_Amu3D (d=3), written term by term as printed."""
-    M, A, S = mats if mats is not None else iga1d.matrices(p, n)
-    M, A, S = sp.csr_matrix(M), sp.csr_matrix(A), sp.csr_matrix(S)
-    At = A.T.tocsr()
-    K = lambda *ms: _kron_all(list(ms))  # noqa: E731
+    """eq:matr_Amu (d=2) / eq:matr_Amu3D (d=3), written term by term as printed.
+
+    Each Kronecker factor in position l is the 1D matrix of direction l (the same matrix in
+    every position on a uniform mesh; ``mats`` overrides it there).
+    """
+    ns = axis_counts(d, n)
+    if mats is not None:
+        per = [tuple(sp.csr_matrix(x) for x in mats)] * d
+    else:
+        per = [tuple(sp.csr_matrix(x) for x in iga1d.matrices(p, ns[l])) for l in range(d)]
+
+    def K(*letters):
+        """The Kronecker product of the named 1D matrices, letter l acting along x_{l+1}."""
+        fs = []
+        for l, c in enumerate(letters):
+            M, A, S = per[l]
+            fs.append({"M": M, "A": A, "T": A.T.tocsr(), "S": S}[c])
+        return _kron_all(fs)
+    # letters: M, S, A, and T for A^T, in the order of the printed factors
     if d == 2:
-        curl = sp.bmat([[K(M, S), -K(At, A)],
-                        [-K(A, At), K(S, M)]], format="csr")
-        div = sp.bmat([[K(S, M), K(A, At)],
-                       [K(At, A), K(M, S)]], format="csr")
+        curl = sp.bmat([[K("M", "S"), -K("T", "A")],
+                        [-K("A", "T"), K("S", "M")]], format="csr")
+        div = sp.bmat([[K("S", "M"), K("A", "T")],
+                       [K("T", "A"), K("M", "S")]], format="csr")
     elif d == 3:
         curl = sp.bmat([
-            [K(M, M, S) + K(M, S, M), -K(At, A, M), -K(At, M, A)],
-            [-K(A, At, M), K(S, M, M) + K(M, M, S), -K(M, At, A)],
-            [-K(A, M, At), -K(M, A, At), K(S, M, M) + K(M, S, M)],
+            [K("M", "M", "S") + K("M", "S", "M"), -K("T", "A", "M"), -K("T", "M", "A")],
+            [-K("A", "T", "M"), K("S", "M", "M") + K("M", "M", "S"), -K("M", "T", "A")],
+            [-K("A", "M", "T"), -K("M", "A", "T"), K("S", "M", "M") + K("M", "S", "M")],
         ], format="csr")
         div = sp.bmat([
-            [K(S, M, M), K(A, At, M), K(A, M, At)],
-            [K(At, A, M), K(M, S, M), K(M, A, At)],
-            [K(At, M, A), K(M, At, A), K(M, M, S)],
+            [K("S", "M", "M"), K("A", "T", "M"), K("A", "M", "T")],
+            [K("T", "A", "M"), K("M", "S", "M"), K("M", "A", "T")],
+            [K("T", "M", "A"), K("M", "T", "A"), K("M", "M", "S")],
         ], format="csr")
     else:
         raise ValueError("d must be 2 or 3")
@@ -207,16 +239,20 @@ def sine_field(ks):
 
 
 def _grid_points(d, n, nq, rows0=None):
-    x, _ = iga1d.gauss_points(n, nq)
-    x0 = x if rows0 is None else x[rows0]
-    grids = np.meshgrid(*([x0] + [x] * (d - 1)), indexing="ij")
+    ns = axis_counts(d, n)
+    xs = [iga1d.gauss_points(ns[l], nq)[0] for l in range(d)]
+    if rows0 is not None:
+        xs[0] = xs[0][rows0]
+    grids = np.meshgrid(*xs, indexing="ij")
     return [g.ravel() for g in grids]
 
 
 def _chunks(d, n, nq, budget=1_500_000):
     """Slices of the x_1 Gauss points so that each chunk holds about ``budget`` points."""
-    Q = n * nq
-    step = max(1, budget // (Q ** (d - 1)))
+    ns = axis_counts(d, n)
+    Q = ns[0] * nq
+    rest = int(np.prod([v * nq for v in ns[1:]]))
+    step = max(1, budget // rest)
     return [slice(s, min(Q, s + step)) for s in range(0, Q, step)]
 
 

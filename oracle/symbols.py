@@ -34,13 +34,15 @@ def s_sym(p, theta):
     return -c[0] - 2 * sum(c[k] * np.cos(k * theta) for k in range(1, p + 1))
 
 
-def symbol_2d(p, alpha, beta, t1, t2):
-    """The 2x2 symbol f^{p,alpha,beta}(t1, t2) of eq:f2D, shape [..., 2, 2]."""
+def symbol_2d(p, alpha, beta, t1, t2, nu=(1.0, 1.0)):
+    """The 2x2 symbol f^{p,alpha,beta}(t1, t2) of eq:f2D (Theorem 5.1, n_l = n nu_l), shape
+    [..., 2, 2]: the M (x) S terms carry nu_2 / nu_1, the S (x) M terms nu_1 / nu_2."""
     m1, m2 = m_sym(p, t1), m_sym(p, t2)
     s1, s2 = s_sym(p, t1), s_sym(p, t2)
     a1, a2 = a_sym(p, t1), a_sym(p, t2)
-    f11 = alpha * m1 * s2 + beta * s1 * m2
-    f22 = alpha * s1 * m2 + beta * m1 * s2
+    r21, r12 = nu[1] / nu[0], nu[0] / nu[1]
+    f11 = alpha * r21 * m1 * s2 + beta * r12 * s1 * m2
+    f22 = alpha * r12 * s1 * m2 + beta * r21 * m1 * s2
     f12 = -(alpha - beta) * a1 * a2
     return np.stack([np.stack([f11, f12], -1), np.stack([f12, f22], -1)], -2)
 
@@ -56,30 +58,39 @@ def eig_2d_closed(p, alpha, beta, t1, t2):
     return 0.5 * ((alpha + beta) * lp - root), 0.5 * ((alpha + beta) * lp + root)
 
 
-def symbol_3d(p, alpha, beta, t1, t2, t3):
-    """The 3x3 symbol of eq:f3D with gamma_i = delta_i = 1, shape [..., 3, 3]."""
+def symbol_3d(p, alpha, beta, t1, t2, t3, nu=(1.0, 1.0, 1.0)):
+    """The 3x3 symbol of eq:f3D (Theorem 5.5, n_l = n nu_l), shape [..., 3, 3], with
+    gamma_i = nu_i^2 / (nu_1 nu_2 nu_3) weighting the terms whose S acts along x_i and
+    delta_i = 1 / nu_i the coupling term whose M acts along x_i."""
     m = [m_sym(p, t) for t in (t1, t2, t3)]
     s = [s_sym(p, t) for t in (t1, t2, t3)]
     a = [a_sym(p, t) for t in (t1, t2, t3)]
-    smm, msm, mms = s[0] * m[1] * m[2], m[0] * s[1] * m[2], m[0] * m[1] * s[2]
+    vol = nu[0] * nu[1] * nu[2]
+    g = [nu[i] ** 2 / vol for i in range(3)]
+    dl = [1.0 / nu[i] for i in range(3)]
+    smm, msm, mms = g[0] * s[0] * m[1] * m[2], g[1] * m[0] * s[1] * m[2], g[2] * m[0] * m[1] * s[2]
     f11 = beta * smm + alpha * msm + alpha * mms
     f22 = alpha * smm + beta * msm + alpha * mms
     f33 = alpha * smm + alpha * msm + beta * mms
-    f12 = -(alpha - beta) * a[0] * a[1] * m[2]
-    f13 = -(alpha - beta) * a[0] * m[1] * a[2]
-    f23 = -(alpha - beta) * m[0] * a[1] * a[2]
+    f12 = -(alpha - beta) * dl[2] * a[0] * a[1] * m[2]
+    f13 = -(alpha - beta) * dl[1] * a[0] * m[1] * a[2]
+    f23 = -(alpha - beta) * dl[0] * m[0] * a[1] * a[2]
     rows = [np.stack([f11, f12, f13], -1), np.stack([f12, f22, f23], -1), np.stack([f13, f23, f33], -1)]
     return np.stack(rows, -2)
 
 
-def laplacian_sym(p, *thetas):
-    """Scalar IgA Laplacian symbol: eq:lapl2D for two angles, eq:lapl3D for three."""
+def laplacian_sym(p, *thetas, nu=None):
+    """Scalar IgA Laplacian symbol: eq:lapl2D for two angles, eq:lapl3D for three; with nu the
+    weighted forms of Sections 5.1 / 5.2 (2D: nu_2/nu_1 m s + nu_1/nu_2 s m; 3D: gamma_l)."""
     d = len(thetas)
+    nu = (1.0,) * d if nu is None else tuple(nu)
     m = [m_sym(p, t) for t in thetas]
     s = [s_sym(p, t) for t in thetas]
+    vol = float(np.prod(nu))
     out = 0.0
     for l in range(d):
-        term = 1.0
+        # weight of the term with S along x_l: nu_l^2 / prod(nu) (2D: nu_l / nu_other)
+        term = nu[l] ** 2 / vol
         for k in range(d):
             term = term * (s[k] if k == l else m[k])
         out = out + term
@@ -87,16 +98,21 @@ def laplacian_sym(p, *thetas):
 
 
 def grid(m, d):
-    """The grid Gamma of Section 5.3: theta_k = k pi / m, k = 1..m in each direction."""
-    t = np.arange(1, m + 1) * np.pi / m
-    return np.meshgrid(*([t] * d), indexing="ij")
+    """The grid Gamma of Section 5.3: theta_k = k pi / m_l, k = 1..m_l in direction l (m may be
+    one size for every direction or one per direction)."""
+    ms = (m,) * d if np.isscalar(m) else tuple(m)
+    ts = [np.arange(1, ml + 1) * np.pi / ml for ml in ms]
+    return np.meshgrid(*ts, indexing="ij")
 
 
-def sampled_eigs(d, p, alpha, beta, m):
+def sampled_eigs(d, p, alpha, beta, m, nu=None):
     """Lambda_1..Lambda_d of Section 5.3: eigenvalues of the symbol at every point of Gamma.
 
-    Returns an array [m^d, d], each row ascending (Lambda_i is column i).
+    Returns an array [prod m_l, d], each row ascending (Lambda_i is column i).  ``nu`` selects
+    the weighted symbol of an anisotropic mesh (its grid then has m_l = n_l + p - 2 points in
+    direction l).
     """
     g = grid(m, d)
-    f = symbol_2d(p, alpha, beta, *g) if d == 2 else symbol_3d(p, alpha, beta, *g)
+    nu = (1.0,) * d if nu is None else tuple(nu)
+    f = symbol_2d(p, alpha, beta, *g, nu=nu) if d == 2 else symbol_3d(p, alpha, beta, *g, nu=nu)
     return np.linalg.eigvalsh(f.reshape(-1, d, d))

@@ -119,3 +119,49 @@ def test_block_diagonal_cut(d, p, n):
         sl = slice(c * N, (c + 1) * N)
         np.testing.assert_array_equal(D.toarray()[sl, sl], Ad[sl, sl])
     assert abs(D).sum() < abs(A).sum()
+
+
+# ---- anisotropic meshes (per-direction interval counts, Section 5)
+
+@pytest.mark.parametrize("d,ns,p", [(2, (5, 9), 2), (2, (8, 3), 3), (3, (3, 5, 4), 2)])
+def test_anisotropic_kron_form_equals_bilinear_form(d, ns, p):
+    """The printed Kronecker form with the 1D matrices of each direction in their positions equals
+    the bilinear form evaluated by quadrature on the anisotropic tensor mesh."""
+    alpha, beta = 0.7, 2.5
+    Aq = assemble.galerkin_quadrature(d, p, ns, alpha, beta)
+    Ak = assemble.galerkin_kron(d, p, ns, alpha, beta)
+    assert Aq.shape[0] == assemble.dofs(d, p, ns)
+    assert abs(Aq - Ak).max() <= 1e-13 * abs(Aq).max()
+
+
+def test_anisotropic_axis_swap():
+    """Swapping x_1 and x_2 (and the two components) maps the bilinear form on an (n_1, n_2)
+    mesh onto the one on (n_2, n_1): curl changes sign, div is unchanged."""
+    p, n1, n2 = 3, 6, 10
+    A12 = assemble.galerkin_kron(2, p, (n1, n2), 1.3, 0.4).toarray()
+    A21 = assemble.galerkin_kron(2, p, (n2, n1), 1.3, 0.4).toarray()
+    m1, m2 = n1 + p - 2, n2 + p - 2
+    N = m1 * m2
+    perm = np.empty(2 * N, dtype=int)  # new index (c', j, i) <- old (c, i, j), c' = 1 - c
+    for c in range(2):
+        for i in range(m1):
+            for j in range(m2):
+                perm[(1 - c) * N + j * m1 + i] = c * N + i * m2 + j
+    np.testing.assert_allclose(A12[np.ix_(perm, perm)], A21, rtol=0, atol=1e-14 * np.abs(A12).max())
+
+
+def test_anisotropic_uniform_tuple_and_loewner_bounds():
+    """(n, n) gives the isotropic matrix; on an anisotropic mesh A^curl + A^div = blockdiag(K)
+    and min(alpha,beta) K <= A <= max(alpha,beta) K still hold (matrix form of Thm 5.2)."""
+    p = 2
+    np.testing.assert_array_equal(assemble.galerkin_kron(2, p, (7, 7), 1.0, 0.3).toarray(),
+                                  assemble.galerkin_kron(2, p, 7, 1.0, 0.3).toarray())
+    ns, alpha, beta = (4, 9), 1.0, 0.05
+    curl, div = assemble.galerkin_kron(2, p, ns, 1.0, 1.0, parts=True)
+    K = (curl + div).toarray()
+    N = K.shape[0] // 2
+    assert np.abs(K[:N, N:]).max() <= 1e-14 * np.abs(K).max()
+    A = assemble.galerkin_kron(2, p, ns, alpha, beta).toarray()
+    import scipy.linalg as sla
+    ev = sla.eigh(A, K, eigvals_only=True)
+    assert ev.min() >= beta * (1 - 1e-10) and ev.max() <= alpha * (1 + 1e-10)

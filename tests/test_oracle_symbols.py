@@ -111,3 +111,38 @@ def test_3d_one_third_of_spectrum_near_zero_for_small_beta():
     ev = np.linalg.eigvalsh(A)
     frac = np.mean(ev < 0.02 * ev.max())
     assert 0.23 < frac < 0.43, frac
+
+
+# ---- anisotropic meshes n_l = n nu_l (Section 5, Theorems 5.1 / 5.5)
+
+@pytest.mark.parametrize("d,ns,beta", [(2, (20, 40), 0.5), (2, (36, 12), 0.01), (3, (6, 12, 9), 0.5)])
+def test_anisotropic_eigenvalues_follow_weighted_symbol(d, ns, beta):
+    """Sorted eig(n^{d-2} A_n) for n = n nu against the sorted weighted symbol sampled on the
+    per-direction grid (m_l points along x_l); the isotropic symbol of the same mesh size does
+    not match, so a wrong weight or a swapped direction fails."""
+    p = 3
+    n = min(ns)
+    nu = tuple(v / n for v in ns)
+    ms = tuple(v + p - 2 for v in ns)
+    A = assemble.galerkin_kron(d, p, ns, 1.0, beta).toarray() * n ** (d - 2)
+    ev = np.sort(np.linalg.eigvalsh(A))
+    samp = np.sort(symbols.sampled_eigs(d, p, 1.0, beta, ms, nu=nu).ravel())
+    assert ev.size == samp.size
+    err = np.abs(ev - samp) / samp.max()
+    assert np.median(err) < 0.01 and np.quantile(err, 0.95) < 0.05
+    iso = np.sort(symbols.sampled_eigs(d, p, 1.0, beta, ms).ravel())
+    assert np.median(np.abs(ev - iso) / iso.max()) > 2 * np.median(err)
+
+
+@pytest.mark.parametrize("d,nu", [(2, (1.0, 3.0)), (3, (2.0, 1.0, 0.5))])
+def test_weighted_symbol_bounds(d, nu):
+    """min(alpha,beta) L_p <= lambda_i(f) <= max(alpha,beta) L_p with the weighted Laplacian
+    symbol (Theorems 5.2 / 5.6 on anisotropic meshes), equality at alpha = beta."""
+    p, beta, mg = 3, 0.02, 14
+    g = symbols.grid(mg, d)
+    lam = symbols.sampled_eigs(d, p, 1.0, beta, mg, nu=nu)
+    L = symbols.laplacian_sym(p, *g, nu=nu).ravel()
+    sc = np.abs(lam).max()
+    assert np.all(beta * L[:, None] <= lam + 1e-13 * sc) and np.all(lam <= L[:, None] + 1e-13 * sc)
+    lam1 = symbols.sampled_eigs(d, p, 0.7, 0.7, mg, nu=nu)
+    np.testing.assert_allclose(lam1, np.repeat(0.7 * L[:, None], d, 1), rtol=1e-12, atol=1e-14 * sc)
