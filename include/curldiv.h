@@ -106,7 +106,9 @@ typedef struct {
   int inner_maxit;    /* FP32-IR: inner iteration cap per refinement step (4000)  */
   int max_outer;      /* FP32-IR: refinement steps before giving up (default 30)  */
   int smoother_degree;/* MG: Chebyshev smoothing steps per visit (default 2)      */
-  int mg_m_min;       /* MG: stop coarsening at m <= mg_m_min (default 3)         */
+  int mg_m_min;       /* MG: stop coarsening at m <= mg_m_min and invert the
+                          coarsest level densely (default 0: 16 for CD_PC_MG in
+                          2D, else 3)                                            */
   int use_graphs;     /* capture the Krylov iteration in CUDA graphs (default 1)  */
   int chunk;          /* iterations per graph launch / host convergence poll (8)  */
   double mixed_switch_ratio; /* FP32-IR: parameter ratio above which the inner
@@ -164,6 +166,24 @@ CD_API const char* cd_last_error(void);
  * cudaStream_t (NULL = legacy default stream).  opt == NULL selects defaults. */
 CD_API cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha,
                            double beta, const cd_options* opt, void* cuda_stream);
+
+/* cd_create for an anisotropic mesh (Section 5: n_l = nu_l n intervals along x_l, the
+ * spline space the tensor product of the 1D spaces of each direction).  n[0..d-1] are
+ * the per-direction interval counts (host array of d ints, read during the call), so
+ * component c has m_1 ... m_d unknowns, m_l = n[l] + p - 2, and a right-hand side is
+ * [d][m_1]...[m_d] (x_d fastest), d prod_l m_l doubles.  The operator is eq:matr_Amu /
+ * eq:matr_Amu3D with the 1D matrices of direction l in the l-th Kronecker position.
+ * Offered: cd_apply, cd_apply_f32, cd_solve, cd_solve_ext, cd_solve_host, cd_lanczos
+ * and cd_precond, with precond CD_PC_NONE or CD_PC_FD_D (fast diagonalisation of the
+ * block diagonal with each direction's generalized eigenbasis); the residual is
+ * evaluated in FP64 (ext_residual, emulated_fp64, fd_tensor_cores and autotune are
+ * ignored: the handle uses one banded pass per direction and SIMT FD transforms).
+ * opt == NULL selects defaults with CD_PC_NONE.  CD_EINVAL for d not 2 or 3, p < 1,
+ * n NULL, any m_l < 2, d prod m_l >= 2^31, a bad parameter, or another precond; the
+ * multigrid entry points (cd_levels returns 0, cd_restrict, cd_prolong, cd_get_bands,
+ * cd_get_eig) reject such a handle. */
+CD_API cd_status cd_create_aniso(cd_solver* out, int d, int p, const int* n, double alpha,
+                                 double beta, const cd_options* opt, void* cuda_stream);
 CD_API cd_status cd_destroy(cd_solver h);
 
 /* y = A w for nrhs right-hand sides (matrix-free, sum-factorised; eq:matr_Amu /

@@ -94,6 +94,18 @@ int launch_apply(int d, int m, int P, const T* bands /*M,A,S*/, const T* w, T* y
                  const T* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
                  const int* active, T* scratch, cudaStream_t s, const Epi<T>* epi = nullptr);
 
+// y = A w (mode 0) or rhs - A w (mode 1) on an anisotropic mesh: ma[l] unknowns per component
+// along x_l, band[l] the [3][ma[l]][2P+1] row-major (M, A, S) bands of direction l; scratch holds
+// 6 (d = 2) or 18 (d = 3) arrays of [B][prod ma] plus a [B][N] buffer.
+template <typename T>
+int launch_apply_aniso(int d, const int* ma, int P, const T* const* band, const T* w, T* y,
+                       const T* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                       const int* active, T* scratch, cudaStream_t s);
+// FD-D scaling on an anisotropic mesh: z /= sum_l c_{comp,l} lam_l[k_l] (eigen-coordinates)
+template <typename T>
+void launch_fd_scale_aniso(int d, const int* ma, const T* const* lam, int B, const double* alpha,
+                           const double* beta, T* z, const int* active, cudaStream_t s);
+
 // Central-stencil registry for the 2D apply: `bands_dev` is the start of a level's band
 // block ([3][m][W] row-major, then [3][W][m] k-major); rows [lo, hi) equal `central`
 // ([3][W]: M, A, S).

@@ -1186,6 +1186,7 @@ static int apply3d_multipass(int m, int P, const T* bands, const T* w, T* y, int
   return 0;
 }
 
+
 // ------------------------------------------------------------------ 3D fused apply
 // One CTA: an (x_3, x_2) tile of 32 x T2 points and a chunk of output planes [k_lo, k_hi)
 // along x_1.  It marches through the input planes q = k_lo - P .. k_hi + P - 1; for each plane
@@ -1497,6 +1498,219 @@ __global__ void __launch_bounds__(256) post3d_kernel(long long N, const T* __res
   if (dotp) {
     const double s = block_sum(acc);
     if (threadIdx.x == 0) dotp[(size_t)b * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// ------------------------------------------------------------------ anisotropic meshes
+// Section 5: n_l = nu_l n intervals along x_l, so every direction has its own m_l and its own 1D
+// bands.  The operator is the same sum of Kronecker products (eq:matr_Amu / eq:matr_Amu3D), each
+// factor in position l being the 1D matrix of direction l; it is applied by one banded pass per
+// direction (d = 2: six intermediate arrays, d = 3: nine and nine), a thread per grid point.
+template <typename T>
+__global__ void __launch_bounds__(256) aniso_pass_kernel(AxisParams<T> prm, int npts, int stride,
+                                                         int ma, int P, const T* __restrict__ bands,
+                                                         const double* __restrict__ alpha,
+                                                         const double* __restrict__ beta,
+                                                         const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int W = 2 * P + 1;
+  __shared__ T s_cf[4];
+  if (threadIdx.x == 0) {
+    s_cf[0] = T(1);
+    s_cf[1] = T(alpha[b]);
+    s_cf[2] = T(beta[b]);
+    s_cf[3] = T(alpha[b] - beta[b]);
+  }
+  __syncthreads();
+  for (int pt = blockIdx.x * blockDim.x + threadIdx.x; pt < npts; pt += gridDim.x * blockDim.x) {
+    const int ia = (pt / stride) % ma;
+    const int k0 = max(0, P - ia), k1 = min(W - 1, ma - 1 - ia + P);
+    for (int o = 0; o < prm.nout; ++o) {
+      T acc = 0;
+      for (int t = 0; t < prm.nt[o]; ++t) {
+        const AxisTerm tm = prm.t[o][t];
+        const T* in = prm.in[tm.src] + (long long)b * prm.in_bs[tm.src] + pt;
+        const T* band = bands + ((size_t)tm.band * ma + ia) * W;
+        T s = 0;
+        for (int k = k0; k <= k1; ++k) s += band[k] * in[(long long)(k - P) * stride];
+        acc += s_cf[tm.coef] * s;
+      }
+      prm.out[o][(long long)b * prm.out_bs[o] + pt] = acc;
+    }
+  }
+}
+
+// y = A w on an anisotropic mesh: ma[l] unknowns per component along x_l, band[l] the [3][ma[l]][W]
+// row-major (M, A, S) bands of direction l.  Scratch: 6 (d = 2) or 18 (d = 3) arrays of
+// [B][prod ma] plus, for mode 1, one [B][N] buffer.  Modes: 0 (y = A w, optional w^T y
+// partials), 1 (y = rhs - A w, optional y^T y partials).
+template <typename T>
+int launch_apply_aniso(int d, const int* ma, int P, const T* const* band, const T* w, T* y,
+                       const T* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
+                       const int* active, T* scratch, cudaStream_t s) {
+  if (mode > 1) return 1;
+  const int npc = d == 2 ? ma[0] * ma[1] : ma[0] * ma[1] * ma[2];  // points per component
+  const long long N = (long long)d * npc;
+  const int nint = d == 2 ? 6 : 18;
+  T* yt = mode == 1 ? scratch + (long long)nint * npc * B : y;
+  const dim3 grid((unsigned)std::min<long long>((npc + 255) / 256, 4096), B);
+  const int M_ = 0, A_ = 1, S_ = 2, one = 0, al = 1, be = 2, ga = 3;
+  (void)one;
+  auto strd = [&](int axis) {
+    int st = 1;
+    for (int l = axis + 1; l < d; ++l) st *= ma[l];
+    return st;
+  };
+  if (d == 2) {
+    // x_2 pass: PM_c, PS_c, PA_c grouped by the x_1 operator they feed
+    AxisParams<T> q{};
+    q.in[0] = w;
+    q.in[1] = w + npc;
+    q.in_bs[0] = q.in_bs[1] = N;
+    q.nout = 6;
+    for (int o = 0; o < 6; ++o) {
+      q.out[o] = scratch + (long long)o * npc * B;
+      q.out_bs[o] = npc;
+      q.nt[o] = 1;
+    }
+    q.t[0][0] = {0, S_, al};  // y1: M1 [alpha S2 w1]
+    q.t[1][0] = {0, M_, be};  //     S1 [beta M2 w1]
+    q.t[2][0] = {1, A_, ga};  //     A1 [gamma A2 w2]
+    q.t[3][0] = {1, S_, be};  // y2: M1 [beta S2 w2]
+    q.t[4][0] = {1, M_, al};  //     S1 [alpha M2 w2]
+    q.t[5][0] = {0, A_, ga};  //     A1 [gamma A2 w1]
+    aniso_pass_kernel<T><<<grid, 256, 0, s>>>(q, npc, strd(1), ma[1], P, band[1], c.alpha, c.beta,
+                                              active);
+    AxisParams<T> r{};
+    for (int i = 0; i < 6; ++i) {
+      r.in[i] = scratch + (long long)i * npc * B;
+      r.in_bs[i] = npc;
+    }
+    r.nout = 2;
+    for (int comp = 0; comp < 2; ++comp) {
+      r.out[comp] = yt + comp * npc;
+      r.out_bs[comp] = N;
+      r.nt[comp] = 3;
+      r.t[comp][0] = {comp * 3 + 0, M_, 0};
+      r.t[comp][1] = {comp * 3 + 1, S_, 0};
+      r.t[comp][2] = {comp * 3 + 2, A_, 0};
+    }
+    aniso_pass_kernel<T><<<grid, 256, 0, s>>>(r, npc, strd(0), ma[0], P, band[0], c.alpha, c.beta,
+                                              active);
+    count_launch(2);
+  } else {
+    T* Tm = scratch;
+    T* Pm = scratch + 9LL * npc * B;
+    AxisParams<T> a{};
+    for (int comp = 0; comp < 3; ++comp) {
+      a.in[comp] = w + comp * npc;
+      a.in_bs[comp] = N;
+    }
+    a.nout = 9;
+    for (int X = 0; X < 3; ++X)
+      for (int comp = 0; comp < 3; ++comp) {
+        const int o = X * 3 + comp;
+        a.out[o] = Tm + (long long)o * npc * B;
+        a.out_bs[o] = npc;
+        a.nt[o] = 1;
+        a.t[o][0] = AxisTerm{comp, X, 0};
+      }
+    aniso_pass_kernel<T><<<grid, 256, 0, s>>>(a, npc, strd(2), ma[2], P, band[2], c.alpha, c.beta,
+                                              active);
+    AxisParams<T> q{};
+    for (int i = 0; i < 9; ++i) {
+      q.in[i] = Tm + (long long)i * npc * B;
+      q.in_bs[i] = npc;
+    }
+    auto TI = [](int X, int comp) { return X * 3 + comp; };
+    q.nout = 9;
+    for (int o = 0; o < 9; ++o) {
+      q.out[o] = Pm + (long long)o * npc * B;
+      q.out_bs[o] = npc;
+    }
+    q.nt[0] = 2; q.t[0][0] = {TI(S_, 0), M_, al}; q.t[0][1] = {TI(M_, 0), S_, al};
+    q.nt[1] = 1; q.t[1][0] = {TI(M_, 0), M_, be};
+    q.nt[2] = 2; q.t[2][0] = {TI(M_, 1), A_, ga}; q.t[2][1] = {TI(A_, 2), M_, ga};
+    q.nt[3] = 3; q.t[3][0] = {TI(S_, 1), M_, al}; q.t[3][1] = {TI(M_, 1), S_, be};
+    q.t[3][2] = {TI(A_, 2), A_, ga};
+    q.nt[4] = 1; q.t[4][0] = {TI(M_, 1), M_, al};
+    q.nt[5] = 1; q.t[5][0] = {TI(M_, 0), A_, ga};
+    q.nt[6] = 3; q.t[6][0] = {TI(M_, 2), S_, al}; q.t[6][1] = {TI(S_, 2), M_, be};
+    q.t[6][2] = {TI(A_, 1), A_, ga};
+    q.nt[7] = 1; q.t[7][0] = {TI(M_, 2), M_, al};
+    q.nt[8] = 1; q.t[8][0] = {TI(A_, 0), M_, ga};
+    aniso_pass_kernel<T><<<grid, 256, 0, s>>>(q, npc, strd(1), ma[1], P, band[1], c.alpha, c.beta,
+                                              active);
+    AxisParams<T> r{};
+    for (int i = 0; i < 9; ++i) {
+      r.in[i] = Pm + (long long)i * npc * B;
+      r.in_bs[i] = npc;
+    }
+    r.nout = 3;
+    for (int comp = 0; comp < 3; ++comp) {
+      r.out[comp] = yt + comp * npc;
+      r.out_bs[comp] = N;
+      r.nt[comp] = 3;
+      r.t[comp][0] = {comp * 3 + 0, M_, 0};
+      r.t[comp][1] = {comp * 3 + 1, S_, 0};
+      r.t[comp][2] = {comp * 3 + 2, A_, 0};
+    }
+    aniso_pass_kernel<T><<<grid, 256, 0, s>>>(r, npc, strd(0), ma[0], P, band[0], c.alpha, c.beta,
+                                              active);
+    count_launch(3);
+  }
+  const int nb = partial_blocks(N);
+  if (dotp || mode == 1) {
+    post3d_kernel<T><<<dim3(nb, B), 256, 0, s>>>(N, w, yt, y, rhs, mode, active, dotp, 1, P,
+                                                  band[0], c.alpha, c.beta, Epi<T>{});
+    count_launch();
+  }
+  if (nblk) *nblk = nb;
+  return 0;
+}
+template int launch_apply_aniso<double>(int, const int*, int, const double* const*, const double*,
+                                        double*, const double*, int, int, Coef, double*, int*,
+                                        const int*, double*, cudaStream_t);
+template int launch_apply_aniso<float>(int, const int*, int, const float* const*, const float*,
+                                       float*, const float*, int, int, Coef, double*, int*,
+                                       const int*, float*, cudaStream_t);
+
+// z = s .* z with s = 1 / sum_l c_{comp,l} lambda_l[k_l] (the FD-D scaling of an anisotropic
+// mesh: c_{comp,l} = beta where l = comp, else alpha; lambda_l the generalized eigenvalues of
+// direction l), z in the eigen-coordinates of every direction.
+template <typename T>
+__global__ void __launch_bounds__(256) fd_scale_aniso_kernel(int d, int m0, int m1, int m2,
+                                                             const T* __restrict__ lam0,
+                                                             const T* __restrict__ lam1,
+                                                             const T* __restrict__ lam2,
+                                                             const double* __restrict__ alpha,
+                                                             const double* __restrict__ beta,
+                                                             T* __restrict__ z,
+                                                             const int* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int npc = m0 * m1 * (d == 3 ? m2 : 1);
+  const int N = d * npc;
+  const double al = alpha[b], be = beta[b];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int comp = i / npc;
+    int rem = i - comp * npc;
+    double lam[3];
+    if (d == 2) {
+      lam[0] = (double)lam0[rem / m1];
+      lam[1] = (double)lam1[rem % m1];
+    } else {
+      lam[0] = (double)lam0[rem / (m1 * m2)];
+      lam[1] = (double)lam1[(rem / m2) % m1];
+      lam[2] = (double)lam2[rem % m2];
+    }
+    double den = 0.0;
+    for (int l = 0; l < d; ++l) {
+      // the term with S along x_l: its eigenvalue lambda_l, M elsewhere (eigenvalue 1)
+      den += (l == comp ? be : al) * lam[l];
+    }
+    z[(long long)b * N + i] = (T)((double)z[(long long)b * N + i] / den);
   }
 }
 
@@ -1873,10 +2087,10 @@ __device__ __forceinline__ void ff2_emit(const FF2& yy, long long o1, long long 
   y[o2] = y2;
 }
 
-template <int P>
+template <int P, int MODE>
 __global__ void __launch_bounds__(128, 3) apply2d_ff2_kernel(
     int m, const float2* __restrict__ bandF, StencilFF2 cs, const double* __restrict__ w,
-    double* __restrict__ y, const double* __restrict__ rhs, int mode,
+    double* __restrict__ y, const double* __restrict__ rhs, int /*mode: MODE*/,
     const double* __restrict__ alpha, const double* __restrict__ beta,
     const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
     Epi<double> epi) {
@@ -2023,7 +2237,7 @@ __global__ void __launch_bounds__(128, 3) apply2d_ff2_kernel(
   }
   // ---- axis x_1: lane = column, RS rows per warp: y = M1 PM + S1 PS + A1 PA
   double acc = 0.0, ec1 = 0.0, ec2 = 0.0;
-  if (mode == 2) cheb_coef_cta(epi.lmax[b], epi.step, ec1, ec2);
+  if (MODE == 2) cheb_coef_cta(epi.lmax[b], epi.step, ec1, ec2);
   const int cc = lane, j = c0 + cc;
   const int rb = warp * RS;
   if (j < m) {
@@ -2065,7 +2279,7 @@ __global__ void __launch_bounds__(128, 3) apply2d_ff2_kernel(
 #pragma unroll
       for (int r = 0; r < RS; ++r) {
         const long long o1 = (long long)b * N + (long long)(r0 + rb + r) * m + j;
-        ff2_emit(yy[r], o1, o1 + (long long)m * m, mode, w, y, rhs, epi, ec1, ec2, dotp, acc);
+        ff2_emit(yy[r], o1, o1 + (long long)m * m, MODE, w, y, rhs, epi, ec1, ec2, dotp, acc);
       }
     } else {  // boundary rows (band rows staged in shared memory)
 #pragma unroll 1
@@ -2083,7 +2297,7 @@ __global__ void __launch_bounds__(128, 3) apply2d_ff2_kernel(
           }
         }
         const long long o1 = (long long)b * N + (long long)i * m + j;
-        ff2_emit(yy, o1, o1 + (long long)m * m, mode, w, y, rhs, epi, ec1, ec2, dotp, acc);
+        ff2_emit(yy, o1, o1 + (long long)m * m, MODE, w, y, rhs, epi, ec1, ec2, dotp, acc);
       }
     }
   }
@@ -2096,7 +2310,11 @@ __global__ void __launch_bounds__(128, 3) apply2d_ff2_kernel(
 
 template <int P>
 static void set_ff2_attr() {
-  cudaFuncSetAttribute(apply2d_ff2_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(apply2d_ff2_kernel<P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)FF2Tile<P>::smem);
+  cudaFuncSetAttribute(apply2d_ff2_kernel<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)FF2Tile<P>::smem);
+  cudaFuncSetAttribute(apply2d_ff2_kernel<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)FF2Tile<P>::smem);
 }
 
@@ -2126,8 +2344,16 @@ static bool launch_ff2_P(int m, const StencilHost& sh, const double* w, double* 
   if (!stencil_ff2(sh, cs)) return false;
   dim3 grid((m + G::TC - 1) / G::TC, (m + G::TR - 1) / G::TR, B);
   if (dotp && (long long)grid.x * grid.y > kMaxPartials) return false;
-  apply2d_ff2_kernel<P><<<grid, 128, G::smem, s>>>(m, sh.ffT, cs, w, y, rhs, mode, c.alpha, c.beta,
-                                                   c.gsc, active, dotp, g_epi<double>);
+  // one instantiation per epilogue mode keeps each kernel's code within the instruction cache
+  if (mode == 0)
+    apply2d_ff2_kernel<P, 0><<<grid, 128, G::smem, s>>>(m, sh.ffT, cs, w, y, rhs, mode, c.alpha,
+                                                        c.beta, c.gsc, active, dotp, g_epi<double>);
+  else if (mode == 1)
+    apply2d_ff2_kernel<P, 1><<<grid, 128, G::smem, s>>>(m, sh.ffT, cs, w, y, rhs, mode, c.alpha,
+                                                        c.beta, c.gsc, active, dotp, g_epi<double>);
+  else
+    apply2d_ff2_kernel<P, 2><<<grid, 128, G::smem, s>>>(m, sh.ffT, cs, w, y, rhs, mode, c.alpha,
+                                                        c.beta, c.gsc, active, dotp, g_epi<double>);
   count_launch();
   if (nblk) *nblk = grid.x * grid.y;
   return true;
@@ -2454,4 +2680,21 @@ bool apply_can_fuse(int d, int m, int P, const T* bands, int B) {
 template bool apply_can_fuse<float>(int, int, int, const float*, int);
 template bool apply_can_fuse<double>(int, int, int, const double*, int);
 
+}  // namespace cd
+
+namespace cd {
+template <typename T>
+void launch_fd_scale_aniso(int d, const int* ma, const T* const* lam, int B, const double* alpha,
+                           const double* beta, T* z, const int* active, cudaStream_t s) {
+  const long long N = (long long)d * ma[0] * ma[1] * (d == 3 ? ma[2] : 1);
+  const dim3 grid((unsigned)std::min<long long>((N + 255) / 256, 4096), B);
+  fd_scale_aniso_kernel<T><<<grid, 256, 0, s>>>(d, ma[0], ma[1], d == 3 ? ma[2] : 1, lam[0], lam[1],
+                                                d == 3 ? lam[2] : lam[1], alpha, beta, z, active);
+  count_launch();
+}
+template void launch_fd_scale_aniso<double>(int, const int*, const double* const*, int,
+                                            const double*, const double*, double*, const int*,
+                                            cudaStream_t);
+template void launch_fd_scale_aniso<float>(int, const int*, const float* const*, int, const double*,
+                                           const double*, float*, const int*, cudaStream_t);
 }  // namespace cd

@@ -422,6 +422,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   }
 }
 
+template <typename T>
+static int fd_contract(int m, long long I, long long O, int B, const T* G, const T* in, T* out,
+                       FdScale<T> sc, const int* active, cudaStream_t s);
+
 // out = contraction of `in` along `axis` with the m x m matrix G: out_k = sum_j G[j][k] in_j.
 template <typename T>
 int launch_fd_axis(int d, int m, int axis, int B, const T* G, const T* in, T* out,
@@ -430,6 +434,28 @@ int launch_fd_axis(int d, int m, int axis, int B, const T* G, const T* in, T* ou
   for (int l = axis + 1; l < d; ++l) I *= m;
   long long O = (long long)B * d;
   for (int l = 0; l < axis; ++l) O *= m;
+  return fd_contract<T>(m, I, O, B, G, in, out, sc, active, s);
+}
+
+// The same along `axis` of an anisotropic tensor [B][d][ma[0]]..[ma[d-1]] (G: ma[axis]^2).
+template <typename T>
+int launch_fd_axis_aniso(int d, const int* ma, int axis, int B, const T* G, const T* in, T* out,
+                         const int* active, cudaStream_t s) {
+  long long I = 1;
+  for (int l = axis + 1; l < d; ++l) I *= ma[l];
+  long long O = (long long)B * d;
+  for (int l = 0; l < axis; ++l) O *= ma[l];
+  return fd_contract<T>(ma[axis], I, O, B, G, in, out, FdScale<T>{}, active, s);
+}
+template int launch_fd_axis_aniso<double>(int, const int*, int, int, const double*, const double*,
+                                          double*, const int*, cudaStream_t);
+template int launch_fd_axis_aniso<float>(int, const int*, int, int, const float*, const float*,
+                                         float*, const int*, cudaStream_t);
+
+// outer batch O (B solves), contraction length m, inner extent I
+template <typename T>
+static int fd_contract(int m, long long I, long long O, int B, const T* G, const T* in, T* out,
+                       FdScale<T> sc, const int* active, cudaStream_t s) {
   long long per_solve_outer = O / B;
   constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
   if (I == 1) {

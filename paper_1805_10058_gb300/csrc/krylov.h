@@ -34,6 +34,10 @@ struct FdScale {
 template <typename T>
 int launch_fd_axis(int d, int m, int axis, int B, const T* G, const T* in, T* out,
                    FdScale<T> sc, const int* active, cudaStream_t s);
+// the contraction along `axis` of an anisotropic tensor (ma[l] entries along x_l), no scaling
+template <typename T>
+int launch_fd_axis_aniso(int d, const int* ma, int axis, int B, const T* G, const T* in, T* out,
+                         const int* active, cudaStream_t s);
 
 // z = T^{-1} r with T = I_d (x) T_m (x) ... (eq:kron_precond) by banded Cholesky solves along
 // every axis (the banded factorisation route of Section 6.1).  T_m = L L^T with L lower banded

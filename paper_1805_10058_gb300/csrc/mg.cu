@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <thread>
 
 #include "krylov.h"
 #include "mg.h"
@@ -378,6 +379,47 @@ __global__ void __launch_bounds__(256) coarse_solve_kernel(int nc, const T* __re
   if (lane == 0) x[(size_t)b * nc + i] = s;
 }
 
+// In-place inverse of one SPD matrix per CTA by Gauss-Jordan elimination without pivoting (the
+// pivots of an SPD matrix are positive), FP64; the FP32 copy is written at the end.  A pivot
+// that is not positive sets *bad and the CTA stops.
+__global__ void __launch_bounds__(512) spd_invert_kernel(int n, double* __restrict__ mats,
+                                                         float* __restrict__ mats32,
+                                                         int* __restrict__ bad) {
+  extern __shared__ double colk[];  // column k before the step
+  __shared__ double piv;
+  __shared__ int stop;
+  double* a = mats + (size_t)blockIdx.x * n * n;
+  if (threadIdx.x == 0) stop = 0;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double akk = a[(size_t)k * n + k];
+      if (!(akk > 0.0)) {
+        stop = 1;
+        atomicExch(bad, 1);
+      }
+      piv = 1.0 / akk;
+    }
+    __syncthreads();
+    if (stop) return;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = a[(size_t)i * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      a[(size_t)k * n + j] = j == k ? piv : a[(size_t)k * n + j] * piv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e - i * n;
+      if (i == k) continue;
+      if (j == k)
+        a[e] = -colk[i] * piv;
+      else
+        a[e] -= colk[i] * a[(size_t)k * n + j];
+    }
+    __syncthreads();
+  }
+  float* a32 = mats32 + (size_t)blockIdx.x * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) a32[e] = (float)a[e];
+}
+
 // ------------------------------------------------------------------ host side
 std::vector<double> dense_operator(int d, const Band& M, const Band& A, const Band& S,
                                    double alpha, double beta) {
@@ -498,7 +540,33 @@ cd_status mg_set_params(MgData& mg, int d, int P, int nrhs, const std::vector<do
   const int L = mg.L, nc = mg.nc;
   std::vector<double> inv64((size_t)nrhs * nc * nc);
   std::vector<float> inv32(inv64.size());
-  for (int b = 0; b < nrhs; ++b) {
+  std::vector<char> ok(nrhs, 1);
+  if (nc >= 128) {  // large coarsest level: the matrices go up, the GPU inverts them
+    for (int b = 0; b < nrhs; ++b) {
+      std::vector<double> D = dense_operator(d, mg.hM[L - 1], mg.hA[L - 1], mg.hS[L - 1], alpha[b], beta[b]);
+      if (mg.diag_only) {
+        const int per = nc / d;
+        for (int i = 0; i < nc; ++i)
+          for (int j = 0; j < nc; ++j)
+            if (i / per != j / per) D[(size_t)i * nc + j] = 0.0;
+      }
+      std::copy(D.begin(), D.end(), inv64.begin() + (size_t)b * nc * nc);
+    }
+    CD_CUDA_OK(cudaMemcpyAsync(mg.cinv64, inv64.data(), inv64.size() * 8, cudaMemcpyHostToDevice, s));
+    CD_CUDA_OK(cudaMemsetAsync(mg.tmpB, 0, sizeof(double), s));
+    spd_invert_kernel<<<nrhs, 512, nc * sizeof(double), s>>>(nc, mg.cinv64, mg.cinv32,
+                                                             reinterpret_cast<int*>(mg.tmpB));
+    count_launch();
+    int bad = 0;
+    CD_CUDA_OK(cudaMemcpyAsync(&bad, mg.tmpB, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CD_CUDA_OK(cudaStreamSynchronize(s));  // inv64 (host) goes out of scope
+    if (bad) {
+      set_error("coarsest multigrid matrix is not SPD");
+      return CD_BREAKDOWN;
+    }
+    return CD_OK;
+  }
+  auto one = [&](int b) {
     std::vector<double> D = dense_operator(d, mg.hM[L - 1], mg.hA[L - 1], mg.hS[L - 1], alpha[b], beta[b]);
     if (mg.diag_only) {  // keep the diagonal blocks of the component-major ordering
       const int per = nc / d;
@@ -507,11 +575,28 @@ cd_status mg_set_params(MgData& mg, int d, int P, int nrhs, const std::vector<do
           if (i / per != j / per) D[(size_t)i * nc + j] = 0.0;
     }
     if (!spd_inverse(nc, D)) {
+      ok[b] = 0;
+      return;
+    }
+    std::copy(D.begin(), D.end(), inv64.begin() + (size_t)b * nc * nc);
+  };
+  // one solve's inverse per host thread when the coarsest level is large (each is O(nc^3))
+  const int nth = nc >= 128 ? std::min(nrhs, std::max(1, (int)std::thread::hardware_concurrency())) : 1;
+  if (nth > 1) {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; ++t)
+      th.emplace_back([&, t] {
+        for (int b = t; b < nrhs; b += nth) one(b);
+      });
+    for (auto& x : th) x.join();
+  } else {
+    for (int b = 0; b < nrhs; ++b) one(b);
+  }
+  for (int b = 0; b < nrhs; ++b)
+    if (!ok[b]) {
       set_error("coarsest multigrid matrix is not SPD");
       return CD_BREAKDOWN;
     }
-    std::copy(D.begin(), D.end(), inv64.begin() + (size_t)b * nc * nc);
-  }
   for (size_t i = 0; i < inv64.size(); ++i) inv32[i] = (float)inv64[i];
   CD_CUDA_OK(cudaMemcpyAsync(mg.cinv64, inv64.data(), inv64.size() * 8, cudaMemcpyHostToDevice, s));
   CD_CUDA_OK(cudaMemcpyAsync(mg.cinv32, inv32.data(), inv32.size() * 4, cudaMemcpyHostToDevice, s));

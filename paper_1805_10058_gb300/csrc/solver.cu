@@ -72,6 +72,13 @@ using namespace cd;
 
 struct cd_solver_s {
   int d = 0, p = 0, n = 0, m = 0, P = 0;
+  // anisotropic mesh (Section 5): ma[l] unknowns per component along x_l; bands of direction l
+  // at aoff[l] in bands64 / bands32 ([3][ma[l]][2P+1] row-major); FD-D eigenbases per direction
+  bool aniso = false;
+  int ma[3] = {0, 0, 0};
+  size_t aoff[3] = {0, 0, 0};
+  DevBuf aU64, aUt64, alam64, aU32, aUt32, alam32;  // per direction, concatenated
+  size_t aUoff[3] = {0, 0, 0}, alamoff[3] = {0, 0, 0};
   double alpha0 = 1, beta0 = 1;
   cd_options opt{};
   cudaStream_t s = nullptr;
@@ -151,6 +158,12 @@ static Coef coef_of(cd_solver h) { return Coef{h->alpha.as<double>(), h->beta.as
 template <typename T>
 static int apply_level(cd_solver h, int level, const T* w, T* y, const T* rhs, int mode, int B,
                        double* dotp, int* nblk, const int* active) {
+  if (h->aniso) {
+    const T* base = sizeof(T) == 8 ? (const T*)h->bands64.p : (const T*)h->bands32.p;
+    const T* band[3] = {base + h->aoff[0], base + h->aoff[1], base + h->aoff[2]};
+    return launch_apply_aniso<T>(h->d, h->ma, h->P, band, w, y, rhs, mode, B, coef_of(h), dotp,
+                                 nblk, active, ws_of<T>(h).apply_scratch.template as<T>(), h->s);
+  }
   return launch_apply<T>(h->d, h->ml[level], h->P, bands_of<T>(h, level), w, y, rhs, mode, B,
                          coef_of(h), dotp, nblk, active,
                          ws_of<T>(h).apply_scratch.template as<T>(), h->s);
@@ -195,6 +208,28 @@ static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* 
   }
   if (pc == CD_PC_NONE) {
     vcopy<T>(h->N, B, r, z, active, h->s);
+    return;
+  }
+  if (h->aniso) {  // FD-D with the eigenbases of each direction (the only other kind offered)
+    const bool f64 = sizeof(T) == 8;
+    const T* U = (const T*)(f64 ? h->aU64.p : h->aU32.p);
+    const T* Ut = (const T*)(f64 ? h->aUt64.p : h->aUt32.p);
+    const T* L = (const T*)(f64 ? h->alam64.p : h->alam32.p);
+    const T* lam[3] = {L + h->alamoff[0], L + h->alamoff[1], L + h->alamoff[2]};
+    T* bufs[2] = {w.fa.as<T>(), w.fb.as<T>()};
+    const T* src = r;
+    int pass = 0;
+    for (int a = h->d - 1; a >= 0; --a, ++pass) {  // U_l^T along every direction
+      launch_fd_axis_aniso<T>(h->d, h->ma, a, B, U + h->aUoff[a], src, bufs[pass & 1], active, h->s);
+      src = bufs[pass & 1];
+    }
+    launch_fd_scale_aniso<T>(h->d, h->ma, lam, B, h->alpha.as<double>(), h->beta.as<double>(),
+                             bufs[(pass - 1) & 1], active, h->s);
+    for (int a = h->d - 1; a >= 0; --a, ++pass) {  // U_l along every direction
+      T* dst = a == 0 ? z : bufs[pass & 1];
+      launch_fd_axis_aniso<T>(h->d, h->ma, a, B, Ut + h->aUoff[a], src, dst, active, h->s);
+      src = dst;
+    }
     return;
   }
   if (pc == CD_PC_MG) {
@@ -640,20 +675,30 @@ static cd_status ensure_fd(cd_solver h) {
 namespace cd {
 // Device bytes a handle for (d, p, n) allocates with these options (the estimate the serving
 // runtime admits against; it mirrors the allocations of cd_create and mg_build).
+// Coarsest multigrid size: the option, or (0) 16 for the Chebyshev multigrid in 2D (a dense
+// coarse solve of at most 2 * 16^2 unknowns replaces three launch-bound levels) and 3 otherwise
+// (the paper's strategies P_MIM / P_WL keep its hierarchy, Section 6.1, down to m <= 3).
+static int mg_coarsest(int d, int opt_m_min, int precond) {
+  if (opt_m_min <= 0) return d == 2 && precond == CD_PC_MG ? 16 : 3;
+  return opt_m_min;
+}
+
 size_t solver_bytes(int d, int p, int n, const cd_options& opt) {
   const size_t B = (size_t)std::max(1, opt.max_batch);
   const size_t N = cd_dofs(d, p, n);
   const int m = n + p - 2, W = 2 * p + 1;
   size_t bytes = 0;
-  size_t nl = 0, n3 = 0, n3_1 = 0;
+  size_t nl = 0, n3 = 0, n3_1 = 0, nc = 0;
   for (int ml = m, l = 0;; ++l) {
     nl += 2 * (size_t)3 * ml * W + 8;  // bands of the level
     if (l == 0) n3 = (size_t)ml * ml * ml;
     if (l == 1) n3_1 = (size_t)ml * ml * ml;
-    if (ml <= std::max(1, opt.mg_m_min) || ml / 2 < 1) break;
+    nc = d == 2 ? (size_t)2 * ml * ml : (size_t)3 * ml * ml * ml;
+    if (ml <= mg_coarsest(d, opt.mg_m_min, opt.precond) || ml / 2 < 1) break;
     ml /= 2;
   }
   bytes += nl * 12;
+  bytes += B * nc * nc * 12;  // dense coarsest inverses (FP64 and FP32) per solve
   bytes += B * N * (7 * 8 + 7 * 4 + 8 + 16);  // Krylov workspaces, r64, b64/x64
   if (d == 3) bytes += 21 * n3 * B * 12;
   bytes += 4 * 8 * B * kMaxPartials + 64 * B;
@@ -690,7 +735,7 @@ void cd_default_options(cd_options* o) {
   o->inner_maxit = 4000;
   o->max_outer = 30;
   o->smoother_degree = 2;
-  o->mg_m_min = 3;
+  o->mg_m_min = 0;
   o->use_graphs = 1;
   o->chunk = 8;
   o->mixed_switch_ratio = 1e4;
@@ -726,6 +771,32 @@ uint64_t cd_kernel_launches(void) { return cd::launches(); }
 
 static cd_status ensure_tband(cd_solver h);
 static cd_status ensure_ksmooth(cd_solver h, int kind);
+
+// Per-solve state, Krylov vectors of both precisions and the apply scratch (elements per
+// precision); false when an allocation fails.
+static bool alloc_workspace(cd_solver h, long long scratch_elems) {
+  const int B = h->Bcap;
+  const long long N = h->N;
+  auto al = [&](DevBuf& bfr, size_t bytes) { return bfr.alloc(bytes) == cudaSuccess; };
+  bool ok = al(h->alpha, 8 * B) && al(h->beta, 8 * B);
+  for (auto& x : h->sd) ok = ok && al(x, 8 * B);
+  for (auto& x : h->si) ok = ok && al(x, 4 * B);
+  for (auto& x : h->part) ok = ok && al(x, 8 * (size_t)B * kMaxPartials);
+  ok = ok && al(h->ir_rnorm, 8 * B) && al(h->ir_bnorm2, 8 * B) && al(h->ir_relres, 8 * B) &&
+       al(h->ir_active, 4 * B) && al(h->ir_status, 4 * B) && al(h->ir_outer, 4 * B) &&
+       al(h->ir_inner_total, 4 * B) && al(h->cnt, 64) && al(h->r64, 8 * (size_t)B * N) &&
+       al(h->ir_rrprev, 8 * B) && al(h->ir_grp, 4 * B) && al(h->ir_tol2, 8 * B) &&
+       al(h->ir_m0, 4 * B) && al(h->ir_m1, 4 * B) && al(h->ir_m2, 4 * B);
+  for (int prec = 0; prec < 2; ++prec) {
+    const size_t es = prec == 0 ? 8 : 4;
+    Workspace& w = prec == 0 ? h->w64 : h->w32;
+    const size_t vb = es * (size_t)B * N;
+    ok = ok && al(w.x, vb) && al(w.r, vb) && al(w.z, vb) && al(w.p, vb) && al(w.q, vb) &&
+         al(w.fa, vb) && al(w.fb, vb) &&
+         al(w.apply_scratch, es * (size_t)std::max<long long>(scratch_elems, 1));
+  }
+  return ok;
+}
 
 cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double beta,
                     const cd_options* opt, void* stream) {
@@ -772,7 +843,7 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
   // 1D bands on every level (finest: quadrature; coarser: Galerkin P^T X P)
   Band M, A, S;
   iga_bands(p, n, P, M, A, S);
-  const int m_min = std::max(1, h->opt.mg_m_min);
+  const int m_min = mg_coarsest(d, h->opt.mg_m_min, h->opt.precond);
   for (;;) {
     h->hM.push_back(M);
     h->hA.push_back(A);
@@ -889,29 +960,13 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     if (st != CD_OK) return st;
   }
   // workspace
-  auto al = [&](DevBuf& bfr, size_t bytes) { return bfr.alloc(bytes) == cudaSuccess; };
-  bool ok = al(h->alpha, 8 * B) && al(h->beta, 8 * B);
-  for (auto& x : h->sd) ok = ok && al(x, 8 * B);
-  for (auto& x : h->si) ok = ok && al(x, 4 * B);
-  for (auto& x : h->part) ok = ok && al(x, 8 * (size_t)B * kMaxPartials);
-  ok = ok && al(h->ir_rnorm, 8 * B) && al(h->ir_bnorm2, 8 * B) && al(h->ir_relres, 8 * B) &&
-       al(h->ir_active, 4 * B) && al(h->ir_status, 4 * B) && al(h->ir_outer, 4 * B) &&
-       al(h->ir_inner_total, 4 * B) && al(h->cnt, 64) && al(h->r64, 8 * (size_t)B * N) &&
-       al(h->ir_rrprev, 8 * B) && al(h->ir_grp, 4 * B) && al(h->ir_tol2, 8 * B) &&
-       al(h->ir_m0, 4 * B) && al(h->ir_m1, 4 * B) && al(h->ir_m2, 4 * B);
   const long long scratch3d = (d == 3) ? 21LL * (N / 3) * B : 0;
-  for (int prec = 0; prec < 2; ++prec) {
-    const size_t es = prec == 0 ? 8 : 4;
-    Workspace& w = prec == 0 ? h->w64 : h->w32;
-    const size_t vb = es * (size_t)B * N;
-    ok = ok && al(w.x, vb) && al(w.r, vb) && al(w.z, vb) && al(w.p, vb) && al(w.q, vb) &&
-         al(w.fa, vb) && al(w.fb, vb) && al(w.apply_scratch, es * (size_t)std::max<long long>(scratch3d, 1));
-  }
-  if (!ok) {
+  if (!alloc_workspace(h.get(), scratch3d)) {
     set_error("workspace allocation failed");
     cudaGetLastError();
     return CD_ENOMEM;
   }
+  auto al = [&](DevBuf& bfr, size_t bytes) { return bfr.alloc(bytes) == cudaSuccess; };
   if (h->opt.ext_residual) {  // double-FP64 solution and residual intermediates
     const long long per = ext_scratch_doubles_per_solve(d, m);
     const long long budget = (256LL << 20) / 8;  // doubles of intermediates per launch group
@@ -963,6 +1018,132 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
                            h->w64.q.as<double>(), B, coef_of(h.get()), h->s);
     }
   }
+  if (cudaStreamSynchronize(h->s) != cudaSuccess) {
+    set_error(cudaGetErrorString(cudaGetLastError()));
+    return CD_ECUDA;
+  }
+  *out = h.release();
+  return CD_OK;
+}
+
+cd_status cd_create_aniso(cd_solver* out, int d, int p, const int* n, double alpha, double beta,
+                          const cd_options* opt, void* stream) {
+  if (!out) return CD_EINVAL;
+  *out = nullptr;
+  if ((d != 2 && d != 3) || p < 1 || !n) {
+    set_error("need d in {2,3}, p >= 1 and one interval count per direction");
+    return CD_EINVAL;
+  }
+  long long npc = 1;
+  for (int l = 0; l < d; ++l) {
+    if (n[l] < 1 || n[l] + p - 2 < 2) {
+      set_error("need n_l >= 1 and m_l = n_l+p-2 >= 2 in every direction");
+      return CD_EINVAL;
+    }
+    npc *= n[l] + p - 2;
+  }
+  if (d * npc >= (1LL << 31)) {
+    set_error("d prod_l (n_l+p-2) must be below 2^31");
+    return CD_EINVAL;
+  }
+  if (!(alpha > 0) || !(beta > 0) || !std::isfinite(alpha) || !std::isfinite(beta)) {
+    set_error("alpha and beta must be finite and > 0");
+    return CD_EINVAL;
+  }
+  std::unique_ptr<cd_solver_s> h(new cd_solver_s());
+  h->aniso = true;
+  h->d = d;
+  h->p = p;
+  h->n = n[0];
+  h->P = p;
+  for (int l = 0; l < d; ++l) h->ma[l] = n[l] + p - 2;
+  h->m = h->ma[0];
+  h->alpha0 = alpha;
+  h->beta0 = beta;
+  cd_default_options(&h->opt);
+  h->opt.precond = CD_PC_NONE;
+  if (opt) h->opt = *opt;
+  if (h->opt.max_batch < 1 || h->opt.max_batch > 4096 || h->opt.chunk < 1 || h->opt.maxit < 1 ||
+      !(h->opt.rtol > 0) || h->opt.precision < 0 || h->opt.precision > 1) {
+    set_error("invalid options");
+    return CD_EINVAL;
+  }
+  if (h->opt.precond != CD_PC_NONE && h->opt.precond != CD_PC_FD_D) {
+    set_error("anisotropic meshes: precond must be CD_PC_NONE or CD_PC_FD_D");
+    return CD_EINVAL;
+  }
+  // the banded passes of the anisotropic apply: FP64 residuals and SIMT FD transforms
+  h->opt.ext_residual = 0;
+  h->opt.emulated_fp64 = 0;
+  h->opt.fd_tensor_cores = 0;
+  h->opt.autotune = 0;
+  h->s = static_cast<cudaStream_t>(stream);
+  if (prepare_kernels() != 0) {
+    set_error(cudaGetErrorString(cudaGetLastError()));
+    return CD_ECUDA;
+  }
+  h->N = d * npc;
+  h->Bcap = h->opt.max_batch;
+  const int P = p, W = 2 * P + 1;
+  // 1D bands of every direction ([3][m_l][W] row-major), M and S exactly symmetric, A exactly
+  // skew (upper entries copied to the lower ones), as on a uniform mesh
+  std::vector<double> all, Uall, Utall, lamall;
+  for (int l = 0; l < d; ++l) {
+    Band M, A, S;
+    iga_bands(p, n[l], P, M, A, S);
+    Band* X[3] = {&M, &A, &S};
+    const int ml = h->ma[l];
+    for (int x = 0; x < 3; ++x) {
+      const double sgn = x == 1 ? -1.0 : 1.0;
+      std::vector<double>& v = X[x]->v;
+      for (int i = 0; i < ml; ++i)
+        for (int k = 1; k <= P && i + k < ml; ++k)
+          v[(size_t)(i + k) * W + P - k] = sgn * v[(size_t)i * W + P + k];
+      if (x == 1)
+        for (int i = 0; i < ml; ++i) v[(size_t)i * W + P] = 0.0;
+    }
+    h->aoff[l] = all.size();
+    for (int x = 0; x < 3; ++x) all.insert(all.end(), X[x]->v.begin(), X[x]->v.end());
+    while (all.size() % 4) all.push_back(0.0);
+    if (h->opt.precond == CD_PC_FD_D) {  // S_l U = M_l U Lambda_l, U^T M_l U = I
+      std::vector<double> U, lam;
+      if (!gen_eig(ml, band_to_dense(M), band_to_dense(S), U, lam)) {
+        set_error("generalized eigen-decomposition failed");
+        return CD_EINVAL;
+      }
+      h->aUoff[l] = Uall.size();
+      h->alamoff[l] = lamall.size();
+      Uall.insert(Uall.end(), U.begin(), U.end());
+      for (int i = 0; i < ml; ++i)
+        for (int j = 0; j < ml; ++j) Utall.push_back(U[(size_t)j * ml + i]);
+      lamall.insert(lamall.end(), lam.begin(), lam.end());
+    }
+  }
+  for (int l = d; l < 3; ++l) h->aoff[l] = h->aoff[d - 1];
+  if (upload(h->bands64, all) != cudaSuccess || upload(h->bands32, cast_vec<float>(all)) != cudaSuccess) {
+    set_error("band upload failed");
+    return CD_ECUDA;
+  }
+  if (h->opt.precond == CD_PC_FD_D) {
+    for (int l = d; l < 3; ++l) {
+      h->aUoff[l] = h->aUoff[d - 1];
+      h->alamoff[l] = h->alamoff[d - 1];
+    }
+    if (upload(h->aU64, Uall) != cudaSuccess || upload(h->aUt64, Utall) != cudaSuccess ||
+        upload(h->alam64, lamall) != cudaSuccess || upload(h->aU32, cast_vec<float>(Uall)) != cudaSuccess ||
+        upload(h->aUt32, cast_vec<float>(Utall)) != cudaSuccess ||
+        upload(h->alam32, cast_vec<float>(lamall)) != cudaSuccess) {
+      set_error("eigenbasis upload failed");
+      return CD_ECUDA;
+    }
+  }
+  const long long scratch = (long long)(d == 2 ? 6 : 18) * npc * h->Bcap + h->N * h->Bcap;
+  if (!alloc_workspace(h.get(), scratch)) {
+    set_error("workspace allocation failed");
+    cudaGetLastError();
+    return CD_ENOMEM;
+  }
+  if (cudaMallocHost(&h->h_cnt, 64) != cudaSuccess) return CD_ENOMEM;
   if (cudaStreamSynchronize(h->s) != cudaSuccess) {
     set_error(cudaGetErrorString(cudaGetLastError()));
     return CD_ECUDA;
@@ -1171,8 +1352,12 @@ cd_status cd_precond(cd_solver h, int kind, const void* r, void* z, int nrhs, co
   cd_status st = check_call(h, r, z, nrhs);
   if (st != CD_OK) return st;
   if (kind < CD_PC_NONE || kind > CD_PC_WL) return CD_EINVAL;
+  if (h->aniso && kind != CD_PC_NONE && !(kind == CD_PC_FD_D && h->aU64.p)) {
+    set_error("anisotropic mesh: only CD_PC_NONE, and CD_PC_FD_D on a handle created with it");
+    return CD_EINVAL;
+  }
   std::lock_guard<std::mutex> lk(h->mu);
-  if (kind == CD_PC_FD_D || kind == CD_PC_FD_T) {
+  if (!h->aniso && (kind == CD_PC_FD_D || kind == CD_PC_FD_T)) {
     st = ensure_fd(h);
     if (st != CD_OK) return st;
   }
@@ -1287,7 +1472,7 @@ cd_status cd_get_bands(cd_solver h, int level, double* M, double* A, double* S, 
 }
 
 cd_status cd_get_eig(cd_solver h, int which, double* U, double* lam) {
-  if (!h || (which != 0 && which != 1)) return CD_EINVAL;
+  if (!h || h->aniso || (which != 0 && which != 1)) return CD_EINVAL;
   {
     std::lock_guard<std::mutex> lk(h->mu);
     cd_status st = ensure_fd(h);

@@ -78,6 +78,8 @@ def load(path=LIB_PATH):
         "cd_strerror": (ctypes.c_char_p, [i]),
         "cd_last_error": (ctypes.c_char_p, []),
         "cd_create": (i, [ctypes.POINTER(vp), i, i, i, d, d, ctypes.POINTER(Options), vp]),
+        "cd_create_aniso": (i, [ctypes.POINTER(vp), i, i, ctypes.POINTER(ctypes.c_int), d, d,
+                                ctypes.POINTER(Options), vp]),
         "cd_destroy": (i, [vp]),
         "cd_apply": (i, [vp, vp, vp, i, dp, dp]),
         "cd_apply_f32": (i, [vp, vp, vp, i, dp, dp]),
@@ -232,21 +234,37 @@ def _dev(t, dtype_name):
 
 
 class Solver:
-    """Owns a cd_solver handle for (d, p, n); methods mirror the C entry points."""
+    """Owns a cd_solver handle for (d, p, n); methods mirror the C entry points.  ``n`` is the
+    number of intervals per direction, or a sequence of d per-direction counts (an anisotropic
+    mesh: cd_create_aniso)."""
 
     def __init__(self, d, p, n, alpha=1.0, beta=1.0, stream=None, **opts):
         self.lib = load()
         self.d, self.p, self.n = d, p, n
-        self.m = n + p - 2
-        self.N = cd_dofs(d, p, n)
-        self.opts = default_options(**opts)
+        self.aniso = not np.isscalar(n)
         h = ctypes.c_void_p()
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
         self.stream = stream
-        _check(self.lib.cd_create(ctypes.byref(h), d, p, n, alpha, beta, ctypes.byref(self.opts),
-                                  ctypes.c_void_p(stream)), "cd_create")
+        if self.aniso:
+            ns = [int(v) for v in n]
+            if len(ns) != d:
+                raise ValueError("one interval count per direction")
+            self.ma = [v + p - 2 for v in ns]
+            self.m = self.ma[0]
+            self.N = d * int(np.prod(self.ma))
+            self.opts = default_options(**opts)
+            arr = (ctypes.c_int * d)(*ns)
+            _check(self.lib.cd_create_aniso(ctypes.byref(h), d, p, arr, alpha, beta,
+                                            ctypes.byref(self.opts), ctypes.c_void_p(stream)),
+                   "cd_create_aniso")
+        else:
+            self.m = n + p - 2
+            self.N = cd_dofs(d, p, n)
+            self.opts = default_options(**opts)
+            _check(self.lib.cd_create(ctypes.byref(h), d, p, n, alpha, beta, ctypes.byref(self.opts),
+                                      ctypes.c_void_p(stream)), "cd_create")
         self.h = h
 
     def close(self):

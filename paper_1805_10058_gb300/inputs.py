@@ -8,7 +8,10 @@ import numpy as np
 
 
 def dofs(d, p, n):
-    return d * (n + p - 2) ** d
+    """d (n+p-2)^d, or d prod_l (n_l+p-2) for per-direction interval counts n = (n_1..n_d)."""
+    if np.isscalar(n):
+        return d * (n + p - 2) ** d
+    return d * int(np.prod([v + p - 2 for v in n]))
 
 
 def uniform_rhs(d, p, n, seed, nrhs=1):

@@ -31,8 +31,9 @@ def _rhs(d, p, n, beta):
 
 def gpu_count(d, p, n, beta, pc):
     b = _rhs(d, p, n, beta)
+    # every strategy on the paper's hierarchy (Section 6.1: coarsened to m <= 3 here)
     s = cdl.Solver(d, p, n, 1.0, beta, max_batch=1, precond=pc, precision=cdl.CD_PREC_FP64,
-                   rtol=1e-7, maxit=5000, ext_residual=0)
+                   rtol=1e-7, maxit=5000, ext_residual=0, mg_m_min=3)
     bt = torch.as_tensor(b, device="cuda")
     x = torch.zeros_like(bt)
     st, res = s.cd_solve(bt, x, check=False)

@@ -210,7 +210,7 @@ def test_fd_preconditioners_match_direct_solves(d, p, n):
 
 @pytest.mark.parametrize("d,p,n", [(2, 2, 16), (2, 3, 21), (3, 2, 11)])
 def test_multigrid_transfers_match_prolongator(d, p, n):
-    s = cdl.Solver(d, p, n, max_batch=2, precond=cdl.CD_PC_MG)
+    s = cdl.Solver(d, p, n, max_batch=2, precond=cdl.CD_PC_MG, mg_m_min=3)
     m, mc = s.level_m(0), s.level_m(1)
     P = solvers.block_prolongator(d, m)
     assert P.shape == (d * m ** d, d * mc ** d)
@@ -335,3 +335,20 @@ def test_host_entry_point_and_error_statuses():
         s.cd_apply(dev(b), dev(b), [1.0, -1.0], [1.0, 1.0])
     with pytest.raises(cdl.CurlDivError):
         s.cd_apply(dev(np.zeros(3 * s.N)), dev(np.zeros(3 * s.N)))
+
+
+@pytest.mark.parametrize("p,n,beta", [(2, 16, 0.3), (3, 13, 50.0)])
+def test_mg_single_level_is_the_dense_inverse(p, n, beta):
+    """2D multigrid on a mesh at or below its coarsest size (m <= 16): the V-cycle is the dense
+    coarse solve alone, whose SPD inverse (2 m^2 >= 128 unknowns) is formed on the GPU by
+    Gauss-Jordan elimination, so cd_precond(MG) r = A^{-1} r up to the conditioning."""
+    s = cdl.Solver(2, p, n, max_batch=2, precond=cdl.CD_PC_MG)
+    assert s.cd_levels() == 1
+    R = inputs.uniform_rhs(2, p, n, seed=9, nrhs=2)
+    z = torch.zeros(2 * s.N, dtype=torch.float64, device="cuda")
+    s.cd_precond(cdl.CD_PC_MG, dev(R.ravel()), z, [1.0, 1.0], [beta, 1.0 / beta])
+    Z = host(z).reshape(2, -1)
+    for k, bk in enumerate([beta, 1.0 / beta]):
+        A = oracle_matrix(2, p, n, 1.0, bk)
+        zs = solvers.direct_solve(A, R[k])
+        assert np.linalg.norm(Z[k] - zs) <= 1e-10 * np.linalg.norm(zs), k
