@@ -298,29 +298,34 @@ CD_API uint64_t cd_kernel_launches(void);
 /* ---------------------------------------------------------------- serving runtime
  * Continuous batching of solve requests (the paper has no serving layer; this runs the
  * solves of eq:system for many independent requests on one GPU).  Requests of one shape
- * (d, p, n) share a cached solver; a pool of `workers` threads, each with its own CUDA
- * stream, repeatedly takes the shape whose oldest request is oldest and solves all of its
- * pending requests that fit in `max_batch` right-hand sides in one batched call.  Requests
- * that arrive while their shape is on the GPU join its next batch; different shapes run
- * concurrently.  A shape's solver is admitted when its device footprint fits in
- * `hbm_budget`, evicting idle solvers (least recently used) when needed.  A request's
- * results do not depend on the batch it ran in (every reduction has a fixed order per
- * right-hand side).  Host buffers only; the server copies b at submit and x at poll/wait. */
+ * (d, p, n) share a cached solver whose `max_batch` right-hand-side slots run as a session:
+ * each slot follows the refinement loop of cd_solve on its own schedule, one chunk of Krylov
+ * iterations (cd_options.chunk) per step.  A pool of `workers` threads, each stepping one
+ * shape at a time on that shape's stream, takes the shape that is due (its last step or its
+ * oldest queued request is oldest), admits queued requests into free slots (all right-hand
+ * sides of a request together), runs one step and completes the slots that finished: requests
+ * join and leave between chunks of iterations while the other slots keep running, and
+ * different shapes step concurrently.  A shape's solver is admitted when its device footprint
+ * fits in `hbm_budget`, evicting idle solvers (least recently used) when needed.  A request's
+ * results do not depend on what else runs (every kernel is masked per slot and every
+ * reduction has a fixed order per slot): they equal those of cd_solve_host on the same
+ * right-hand side.  Host buffers only; the server copies b at submit and x at poll/wait. */
 typedef struct cd_server_s* cd_server;
 
 typedef struct {
   size_t hbm_budget;  /* device bytes the cached solvers may hold (0: 80% of free memory) */
-  int workers;        /* concurrent batches, one thread and stream each (default 8)        */
-  int max_batch;      /* right-hand sides per batched solve (default 16)                   */
+  int workers;        /* shapes stepped concurrently, one thread each (default 8)          */
+  int max_batch;      /* session slots (right-hand sides in flight) per shape (default 16) */
   double timeout_s;   /* a request still queued after this many seconds fails with
                          CD_TIMEOUT (0: no limit)                                           */
   cd_options solve;   /* options of every solve (default: cd_default_options, CD_PC_MG)    */
 } cd_server_options;
 
 typedef struct {
-  uint64_t submitted, completed, failed, batches, solves; /* solves = right-hand sides    */
+  uint64_t submitted, completed, failed, batches, solves; /* batches = session steps,
+                                                            solves = right-hand sides     */
   double p50_s, p99_s;  /* latency (submit to completion) of completed requests           */
-  double mean_batch;    /* right-hand sides per batched call                              */
+  double mean_batch;    /* occupied slots per session step                                */
   double solves_per_s;  /* right-hand sides solved / (last completion - first submit)     */
   size_t bytes_in_use;  /* estimated device bytes of the cached solvers                   */
   int handles;          /* cached solvers                                                 */
@@ -343,11 +348,11 @@ CD_API cd_status cd_server_poll(cd_server s, uint64_t ticket, double* x_host, cd
  * ticket then stays valid). */
 CD_API cd_status cd_server_wait(cd_server s, uint64_t ticket, double* x_host, cd_result* res,
                                 double timeout_s);
-/* Cancels a request that has not started (it completes with CD_CANCELLED); CD_EINVAL if it
- * is already on the GPU or unknown. */
+/* Cancels a request that has not been admitted into slots (it completes with CD_CANCELLED);
+ * CD_EINVAL if it is already on the GPU or unknown. */
 CD_API cd_status cd_server_cancel(cd_server s, uint64_t ticket);
 CD_API cd_status cd_server_stats_get(cd_server s, cd_server_stats* out);
-/* Stops the workers after their current batches and frees every cached solver. */
+/* Stops the workers after their current steps and frees every cached solver. */
 CD_API cd_status cd_server_destroy(cd_server s);
 
 /* y = A w for d = 3 (FP64 device vectors, layout as above, one (alpha, beta) for all

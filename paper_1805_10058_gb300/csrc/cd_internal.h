@@ -106,6 +106,13 @@ template <typename T>
 void launch_fd_scale_aniso(int d, const int* ma, const T* const* lam, int B, const double* alpha,
                            const double* beta, T* z, const int* active, cudaStream_t s);
 
+// Serving sessions on a handle (iteration-level continuous batching; the handle's max_batch
+// slots; a handle in session use must not run batched calls meanwhile).
+int sess_busy(cd_solver h);
+cd_status sess_admit(cd_solver h, const double* b_host, double alpha, double beta, int* slot);
+cd_status sess_step(cd_solver h, std::vector<int>& finished);
+cd_status sess_take(cd_solver h, int slot, double* x_host, cd_result* res);
+
 // Central-stencil registry for the 2D apply: `bands_dev` is the start of a level's band
 // block ([3][m][W] row-major, then [3][W][m] k-major); rows [lo, hi) equal `central`
 // ([3][W]: M, A, S).

@@ -137,10 +137,12 @@ __global__ void __launch_bounds__(256) ir_update_kernel(long long N, double* __r
 // ------------------------------------------------------------------ scalar steps
 // State layout (device doubles / ints, each of length B): see PcgState.
 __global__ void cg_init_kernel(int B, PcgState st, const double* part_rr, int nrr,
-                               const double* part_rz, int nrz, const int* outer_active) {
+                               const double* part_rz, int nrz, const int* outer_active,
+                               int keep_others) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
   const bool on = outer_active ? outer_active[b] != 0 : true;
+  if (!on && keep_others) return;  // a solve of a session that is mid-way through its own PCG
   const double rr = psum(part_rr, nrr, b), rz = psum(part_rz, nrz, b);
   st.rr0[b] = rr;
   st.rr[b] = rr;
@@ -535,8 +537,8 @@ void ir_update(long long N, int B, double* x64, const float* e32, const double* 
 }
 static inline int sgrid(int B) { return (B + 127) / 128; }
 void cg_init(int B, PcgState st, const double* prr, int nrr, const double* prz, int nrz,
-             const int* outer_active, cudaStream_t s) {
-  cg_init_kernel<<<sgrid(B), 128, 0, s>>>(B, st, prr, nrr, prz, nrz, outer_active);
+             const int* outer_active, cudaStream_t s, int keep_others) {
+  cg_init_kernel<<<sgrid(B), 128, 0, s>>>(B, st, prr, nrr, prz, nrz, outer_active, keep_others);
   count_launch();
 }
 void cg_alpha(int B, PcgState st, const double* ppq, int npq, cudaStream_t s) {

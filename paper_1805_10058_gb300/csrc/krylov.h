@@ -68,8 +68,10 @@ void ir_cast(long long N, int B, const double* r64, float* r32, const double* rn
              const int* active, cudaStream_t s);
 void ir_update(long long N, int B, double* x64, const float* e32, const double* rnorm,
                const int* active, cudaStream_t s);
+// starts PCG for the solves in outer_active; the others are stopped (active = 0), or left as
+// they are with keep_others (a session's solves that are mid-way through their own PCG)
 void cg_init(int B, PcgState st, const double* prr, int nrr, const double* prz, int nrz,
-             const int* outer_active, cudaStream_t s);
+             const int* outer_active, cudaStream_t s, int keep_others = 0);
 void cg_alpha(int B, PcgState st, const double* ppq, int npq, cudaStream_t s);
 void cg_check(int B, PcgState st, const double* prr, int nrr, const double* prz, int nrz,
               const double* tol2v, int maxit, cudaStream_t s);

@@ -534,6 +534,50 @@ static T* level_scratch(MgData& mg) {
   return (T*)(sizeof(T) == 8 ? mg.scratch64 : mg.scratch32);
 }
 
+// The dense coarsest inverses of the listed solves only (a serving session's new slots); the
+// others keep theirs.  Same arithmetic as mg_set_params for those solves.
+cd_status mg_set_params_slots(MgData& mg, int d, int P, const std::vector<double>& alpha,
+                              const std::vector<double>& beta, const std::vector<int>& slots,
+                              cudaStream_t s) {
+  (void)P;
+  const int L = mg.L, nc = mg.nc;
+  for (int b : slots) {
+    std::vector<double> D = dense_operator(d, mg.hM[L - 1], mg.hA[L - 1], mg.hS[L - 1], alpha[b], beta[b]);
+    if (mg.diag_only) {
+      const int per = nc / d;
+      for (int i = 0; i < nc; ++i)
+        for (int j = 0; j < nc; ++j)
+          if (i / per != j / per) D[(size_t)i * nc + j] = 0.0;
+    }
+    double* dst64 = mg.cinv64 + (size_t)b * nc * nc;
+    float* dst32 = mg.cinv32 + (size_t)b * nc * nc;
+    if (nc >= 128) {
+      CD_CUDA_OK(cudaMemcpyAsync(dst64, D.data(), D.size() * 8, cudaMemcpyHostToDevice, s));
+      CD_CUDA_OK(cudaMemsetAsync(mg.tmpB, 0, sizeof(double), s));
+      spd_invert_kernel<<<1, 512, nc * sizeof(double), s>>>(nc, dst64, dst32,
+                                                            reinterpret_cast<int*>(mg.tmpB));
+      count_launch();
+      int bad = 0;
+      CD_CUDA_OK(cudaMemcpyAsync(&bad, mg.tmpB, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CD_CUDA_OK(cudaStreamSynchronize(s));  // D goes out of scope
+      if (bad) {
+        set_error("coarsest multigrid matrix is not SPD");
+        return CD_BREAKDOWN;
+      }
+    } else {
+      if (!spd_inverse(nc, D)) {
+        set_error("coarsest multigrid matrix is not SPD");
+        return CD_BREAKDOWN;
+      }
+      std::vector<float> D32(D.begin(), D.end());
+      CD_CUDA_OK(cudaMemcpyAsync(dst64, D.data(), D.size() * 8, cudaMemcpyHostToDevice, s));
+      CD_CUDA_OK(cudaMemcpyAsync(dst32, D32.data(), D32.size() * 4, cudaMemcpyHostToDevice, s));
+      CD_CUDA_OK(cudaStreamSynchronize(s));
+    }
+  }
+  return CD_OK;
+}
+
 cd_status mg_set_params(MgData& mg, int d, int P, int nrhs, const std::vector<double>& alpha,
                         const std::vector<double>& beta, cudaStream_t s) {
   // coarsest dense inverses (host, FP64)

@@ -58,6 +58,9 @@ cd_status mg_build(MgData& mg, int d, int P, const std::vector<int>& ml,
                    const std::vector<Band>& hM, const std::vector<Band>& hA,
                    const std::vector<Band>& hS, int B, int deg, const double* bands64,
                    const float* bands32, const std::vector<size_t>& boff);
+cd_status mg_set_params_slots(MgData& mg, int d, int P, const std::vector<double>& alpha,
+                              const std::vector<double>& beta, const std::vector<int>& slots,
+                              cudaStream_t s);
 cd_status mg_set_params(MgData& mg, int d, int P, int nrhs, const std::vector<double>& alpha,
                         const std::vector<double>& beta, cudaStream_t s);
 

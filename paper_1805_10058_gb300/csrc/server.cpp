@@ -1,14 +1,16 @@
 // Serving runtime: continuous batching of solve requests over a pool of CUDA streams.
 //
-// Requests of the same shape (d, p, n) share a cached solver handle (a "bucket").  A pool
-// of worker threads, each driving its own batches, picks the bucket whose oldest pending
-// request is oldest, takes every pending request of that shape that fits in one batch
-// (max_batch right-hand sides, parameters may differ per right-hand side) and solves them
-// in one batched call on the bucket's stream.  Requests that arrive while a bucket's batch
-// is on the GPU join its next batch; batches of different shapes run concurrently.  A new
-// bucket is admitted only when its device footprint fits in the HBM budget, evicting idle
-// buckets (least recently used) if needed.  The solver's reductions have a fixed order per
-// right-hand side, so a request's result does not depend on what it was batched with.
+// Requests of the same shape (d, p, n) share a cached solver handle (a "bucket") whose
+// max_batch right-hand-side slots run as a session: every slot follows the refinement loop on
+// its own schedule, one chunk of Krylov iterations per step.  A pool of worker threads picks the
+// bucket that is due (its last step, or its oldest pending request, is oldest), admits pending
+// requests of that shape into free slots (all right-hand sides of a request together,
+// parameters may differ per right-hand side), runs one step on the bucket's stream and hands
+// back the slots that finished.  So requests join and leave between chunks of iterations while
+// the bucket's other solves keep running, and buckets of different shapes step concurrently.
+// A new bucket is admitted only when its device footprint fits in the HBM budget, evicting idle
+// buckets (least recently used) if needed.  Every kernel is masked per slot and every reduction
+// has a fixed order per slot, so a request's result does not depend on what else runs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,6 +44,7 @@ struct Request {
   std::vector<cd_result> res;
   cd_status status = CD_OK;
   bool done = false, cancelled = false;
+  int remaining = 0;  // right-hand sides still in session slots
   Clock::time_point t_submit, t_done;
 };
 
@@ -53,6 +56,12 @@ struct Bucket {
   bool running = false;
   std::deque<uint64_t> pending;
   Clock::time_point last_used;
+  // session slots of the bucket's handle: owner request and right-hand side index
+  std::vector<std::pair<uint64_t, int>> owner;
+  int busy = 0;
+  // a bucket without a solver whose admission found no room is skipped until then, so that the
+  // buckets holding memory keep stepping and can finish
+  Clock::time_point blocked_until{};
 };
 
 }  // namespace
@@ -69,7 +78,7 @@ struct cd_server_s {
   uint64_t next_id = 1;
   size_t mem_used = 0;
   // statistics
-  uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, solves = 0;
+  uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, solves = 0, slot_steps = 0;
   std::vector<double> latencies;
   Clock::time_point t_first_submit, t_last_done;
   bool any_submit = false;
@@ -126,10 +135,13 @@ void cd_server_s::worker_loop() {
         }
         break;
       }
-      if (bk.running || bk.pending.empty()) continue;
-      const Request& r = *reqs[bk.pending.front()];
-      if (r.t_submit < oldest) {
-        oldest = r.t_submit;
+      if (bk.running || (bk.pending.empty() && bk.busy == 0)) continue;
+      if (!bk.h && now < bk.blocked_until) continue;
+      // a bucket with solves in flight is due by its last step, one with only pending
+      // requests by its oldest request
+      const Clock::time_point due = bk.busy > 0 ? bk.last_used : reqs[bk.pending.front()]->t_submit;
+      if (due < oldest) {
+        oldest = due;
         pick = &bk;
       }
     }
@@ -153,7 +165,9 @@ void cd_server_s::worker_loop() {
         Bucket* lru = nullptr;
         for (auto& kv : buckets) {
           Bucket& o = kv.second;
-          if (o.h && !o.running && o.pending.empty() && (!lru || o.last_used < lru->last_used)) lru = &o;
+          if (o.h && !o.running && o.pending.empty() && o.busy == 0 &&
+              (!lru || o.last_used < lru->last_used))
+            lru = &o;
         }
         if (!lru) break;
         cd_solver hv = lru->h;
@@ -167,8 +181,8 @@ void cd_server_s::worker_loop() {
         cudaStreamDestroy(sv);
         lk.lock();
       }
-      if (mem_used + need > opt.hbm_budget) {  // wait for running batches to free memory
-        cv_work.wait_for(lk, std::chrono::milliseconds(20));
+      if (mem_used + need > opt.hbm_budget) {  // the solvers in use must finish first
+        bk.blocked_until = Clock::now() + std::chrono::milliseconds(20);
         continue;
       }
       bk.running = true;
@@ -193,47 +207,86 @@ void cd_server_s::worker_loop() {
       bk.stream = st;
       bk.bytes = need;
     }
-    // form the batch: pending requests of this shape, in order, while they fit
-    std::vector<Request*> batch;
-    int total = 0;
+    // admission into free session slots (every right-hand side of a request at once, in arrival
+    // order), then one step of the bucket's session: slots join and leave between chunks of
+    // Krylov iterations, so a request does not wait for the solves already running
+    if (bk.owner.empty()) bk.owner.assign(opt.max_batch, std::make_pair(uint64_t(0), -1));
+    std::vector<std::pair<Request*, int>> admit;
+    int free_slots = opt.max_batch - bk.busy;
     while (!bk.pending.empty()) {
       Request* r = reqs[bk.pending.front()].get();
-      if (total + r->nrhs > opt.max_batch) break;
-      total += r->nrhs;
-      batch.push_back(r);
+      if (r->nrhs > free_slots) break;
+      for (int i = 0; i < r->nrhs; ++i) admit.push_back(std::make_pair(r, i));
+      free_slots -= r->nrhs;
+      r->remaining = r->nrhs;
+      r->x.assign((size_t)r->nrhs * cd_dofs(bk.d, bk.p, bk.n), 0.0);
+      r->res.assign(r->nrhs, cd_result{});
       bk.pending.pop_front();
     }
-    if (batch.empty()) continue;
+    bk.busy += (int)admit.size();
     bk.running = true;
     cd_solver h = bk.h;
     const size_t N = cd_dofs(bk.d, bk.p, bk.n);
     lk.unlock();
-    std::vector<double> bb((size_t)total * N), xx((size_t)total * N), al(total), be(total);
-    std::vector<cd_result> res(total);
-    int off = 0;
-    for (Request* r : batch) {
-      std::memcpy(bb.data() + (size_t)off * N, r->b.data(), r->b.size() * sizeof(double));
-      for (int i = 0; i < r->nrhs; ++i) {
-        al[off + i] = r->alpha[i];
-        be[off + i] = r->beta[i];
+    std::vector<std::pair<Request*, cd_status>> failed_adm;
+    for (auto& a : admit) {
+      int slot = -1;
+      const cd_status as = cd::sess_admit(h, a.first->b.data() + (size_t)a.second * N,
+                                          a.first->alpha[a.second], a.first->beta[a.second], &slot);
+      if (as != CD_OK) {
+        failed_adm.push_back(std::make_pair(a.first, as));
+        continue;
       }
-      off += r->nrhs;
+      bk.owner[slot] = std::make_pair(a.first->id, a.second);
     }
-    const cd_status st = cd_solve_host(h, bb.data(), xx.data(), total, al.data(), be.data(), res.data());
+    std::vector<int> fin;
+    const cd_status ss = cd::sess_step(h, fin);
+    std::vector<std::pair<int, cd_result>> outs;
+    for (int slot : fin) {
+      const std::pair<uint64_t, int> own = bk.owner[slot];
+      Request* r = nullptr;
+      {
+        std::lock_guard<std::mutex> lk2(mu);
+        auto it = reqs.find(own.first);
+        if (it != reqs.end()) r = it->second.get();
+      }
+      cd_result res{};
+      std::vector<double> tmp(N);
+      const cd_status ts = cd::sess_take(h, slot, tmp.data(), &res);
+      if (ts != CD_OK) res.status = ts;
+      if (r) std::memcpy(r->x.data() + (size_t)own.second * N, tmp.data(), N * sizeof(double));
+      outs.push_back(std::make_pair(slot, res));
+    }
     lk.lock();
-    off = 0;
-    for (Request* r : batch) {
-      r->x.assign(xx.begin() + (size_t)off * N, xx.begin() + (size_t)(off + r->nrhs) * N);
-      r->res.assign(res.begin() + off, res.begin() + off + r->nrhs);
-      cd_status worst = CD_OK;
-      if (st != CD_OK && st != CD_NOT_CONVERGED && st != CD_BREAKDOWN) worst = st;
-      for (const cd_result& q : r->res)
-        if (q.status != CD_OK && worst == CD_OK) worst = (cd_status)q.status;
-      finish(this, *r, worst);
-      off += r->nrhs;
+    for (auto& f : failed_adm) {  // not admitted: the request fails
+      bk.busy -= 1;
+      if (!f.first->done) finish(this, *f.first, f.second);
+    }
+    for (auto& o : outs) {
+      const std::pair<uint64_t, int> own = bk.owner[o.first];
+      bk.owner[o.first] = std::make_pair(uint64_t(0), -1);
+      bk.busy -= 1;
+      auto it = reqs.find(own.first);
+      if (it == reqs.end()) continue;
+      Request& r = *it->second;
+      r.res[own.second] = o.second;
+      solves += 1;
+      if (--r.remaining == 0 && !r.done) {
+        cd_status worst = CD_OK;
+        for (const cd_result& q : r.res)
+          if (q.status != CD_OK && worst == CD_OK) worst = (cd_status)q.status;
+        finish(this, r, worst);
+      }
+    }
+    if (ss != CD_OK) {  // a failed step: the bucket's solves in flight fail
+      for (size_t k = 0; k < bk.owner.size(); ++k) {
+        if (bk.owner[k].second < 0) continue;
+        auto it = reqs.find(bk.owner[k].first);
+        if (it != reqs.end() && !it->second->done) finish(this, *it->second, ss);
+      }
     }
     batches += 1;
-    solves += (uint64_t)total;
+    slot_steps += (uint64_t)(bk.busy + outs.size());
     bk.running = false;
     bk.last_used = Clock::now();
     cv_done.notify_all();
@@ -402,7 +455,7 @@ cd_status cd_server_stats_get(cd_server S, cd_server_stats* out) {
     out->p50_s = q(0.50);
     out->p99_s = q(0.99);
   }
-  out->mean_batch = S->batches ? (double)S->solves / (double)S->batches : 0.0;
+  out->mean_batch = S->batches ? (double)S->slot_steps / (double)S->batches : 0.0;
   if (S->any_submit && S->solves > 0) {
     const double span = seconds_between(S->t_first_submit, S->t_last_done);
     out->solves_per_s = span > 0 ? (double)S->solves / span : 0.0;

@@ -99,6 +99,15 @@ struct cd_solver_s {
   DevBuf alpha, beta;
   DevBuf sd[6];  // rz rr rr0 alpha beta rzold
   DevBuf si[3];  // active iters status
+  DevBuf sd2[6], si2[3];  // a second PCG state: the FP64 inner group of a serving session
+  // serving session (iteration-level continuous batching): per-slot phase (0 free, 1 pending
+  // admission, 2 outer step due, 3 FP32 inner solve, 4 FP64 inner solve, 5 finished), right-hand
+  // sides and solutions [B][N], device masks, parameters
+  std::vector<int> sp;
+  std::vector<double> s_alpha, s_beta;
+  std::vector<std::chrono::steady_clock::time_point> s_t0;
+  DevBuf s_b, s_x, s_mask;  // s_mask: 4 int arrays [B]
+  std::vector<int> h_mask;
   DevBuf part[4];
   DevBuf ir_rnorm, ir_bnorm2, ir_relres, ir_active, ir_status, ir_outer, ir_inner_total, cnt;
   DevBuf ir_rrprev, ir_grp, ir_tol2, ir_m0, ir_m1, ir_m2;
@@ -114,8 +123,9 @@ struct cd_solver_s {
   bool have_mgD = false;
   std::vector<double> mgD_alpha, mgD_beta;
   std::vector<double> dev_alpha, dev_beta;  // host mirror of the per-solve alpha, beta on the device
-  // CUDA graphs of a chunk of PCG iterations, keyed by (f32, B, pc, flexible, tol, maxit)
-  std::map<std::tuple<int, int, int, int, int, int>, std::pair<cudaGraphExec_t, uint64_t>> graphs;
+  // CUDA graphs of a chunk of PCG iterations, keyed by (f32, B, pc, flexible, arithmetic
+  // flags, maxit, PCG state)
+  std::map<std::tuple<int, int, int, int, int, int, int>, std::pair<cudaGraphExec_t, uint64_t>> graphs;
   std::mutex mu;
   ~cd_solver_s() {
     for (size_t l = 0; l < boff.size(); ++l) {
@@ -129,17 +139,21 @@ struct cd_solver_s {
 
 namespace cd {
 
-static PcgState state_of(cd_solver h) {
+// PCG state 0 (every solve of a batched call; the FP32 group of a session) or 1 (the FP64 group
+// of a session, which runs interleaved with the FP32 one)
+static PcgState state_of(cd_solver h, int which = 0) {
+  DevBuf* sd = which ? h->sd2 : h->sd;
+  DevBuf* si = which ? h->si2 : h->si;
   PcgState st;
-  st.rz = h->sd[0].as<double>();
-  st.rr = h->sd[1].as<double>();
-  st.rr0 = h->sd[2].as<double>();
-  st.alpha = h->sd[3].as<double>();
-  st.beta = h->sd[4].as<double>();
-  st.rzold = h->sd[5].as<double>();
-  st.active = h->si[0].as<int>();
-  st.iters = h->si[1].as<int>();
-  st.status = h->si[2].as<int>();
+  st.rz = sd[0].as<double>();
+  st.rr = sd[1].as<double>();
+  st.rr0 = sd[2].as<double>();
+  st.alpha = sd[3].as<double>();
+  st.beta = sd[4].as<double>();
+  st.rzold = sd[5].as<double>();
+  st.active = si[0].as<int>();
+  st.iters = si[1].as<int>();
+  st.status = si[2].as<int>();
   return st;
 }
 
@@ -294,9 +308,10 @@ static void apply_prec(cd_solver h, int pc, int B, const T* r, T* z, const int* 
 
 // One PCG iteration (all kernels masked by the per-solve active flags).
 template <typename T>
-static void pcg_iteration(cd_solver h, int B, int pc, int flexible, const double* tol2v, int maxit) {
+static void pcg_iteration(cd_solver h, int B, int pc, int flexible, const double* tol2v, int maxit,
+                          int which = 0) {
   Workspace& w = ws_of<T>(h);
-  PcgState st = state_of(h);
+  PcgState st = state_of(h, which);
   const long long N = h->N;
   const int nb = partial_blocks(N);
   int npq = 0;
@@ -314,13 +329,15 @@ static void pcg_iteration(cd_solver h, int B, int pc, int flexible, const double
   xpay<T>(N, B, w.z.as<T>(), w.p.as<T>(), st.beta, st.active, h->s);
 }
 
-// Runs PCG on the workspace of precision T: r holds the right-hand side on entry, x the
-// solution on exit (x_0 = 0).  outer_active masks the solves that take part.
+// Starts PCG on the workspace of precision T for the solves in `outer_active`: r holds the
+// right-hand side, x = 0, z = M r, p = z and the per-solve scalars of PCG state `which`; with
+// keep_others the other solves' state is left untouched (a session's solves mid-way through
+// their own PCG), else they are stopped.  Returns whether the method is flexible.
 template <typename T>
-static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int maxit,
-                         const int* outer_active) {
+static int pcg_begin(cd_solver h, int B, int pc, const int* outer_active, int which,
+                     int keep_others = 0) {
   Workspace& w = ws_of<T>(h);
-  PcgState st = state_of(h);
+  PcgState st = state_of(h, which);
   const long long N = h->N;
   const int nb = partial_blocks(N);
   // a Krylov-smoothed / multigrid or tensor-core (TF32) preconditioner is not an exactly
@@ -335,14 +352,24 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
   apply_prec<T>(h, pc, B, w.r.as<T>(), w.z.as<T>(), outer_active);
   launch_dot<T>(w.r.as<T>(), w.r.as<T>(), N, B, h->part[1].as<double>(), nb, outer_active, h->s);
   launch_dot<T>(w.r.as<T>(), w.z.as<T>(), N, B, h->part[3].as<double>(), nb, outer_active, h->s);
-  cg_init(B, st, h->part[1].as<double>(), nb, h->part[3].as<double>(), nb, outer_active, h->s);
-  vcopy<T>(N, B, w.z.as<T>(), w.p.as<T>(), st.active, h->s);
+  cg_init(B, st, h->part[1].as<double>(), nb, h->part[3].as<double>(), nb, outer_active, h->s,
+          keep_others);
+  vcopy<T>(N, B, w.z.as<T>(), w.p.as<T>(), outer_active, h->s);
+  return flexible;
+}
+
+// Enqueues one chunk of opt.chunk PCG iterations of state `which` (a CUDA graph when enabled)
+// followed by the count of its still-active solves into cnt[0].
+template <typename T>
+static cd_status pcg_chunk(cd_solver h, int B, int pc, int flexible, const double* tol2v, int maxit,
+                           int which) {
+  PcgState st = state_of(h, which);
   const int chunk = std::max(1, h->opt.chunk);
   cudaGraphExec_t exec = nullptr;
   uint64_t nodes = 0;
   if (h->opt.use_graphs) {
     auto key = std::make_tuple((int)(sizeof(T) == 4), B, pc, flexible,
-                               fp64_emulated() + 2 * g_lowp_prec, maxit);
+                               fp64_emulated() + 2 * g_lowp_prec, maxit, which);
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) {
       exec = it->second.first;
@@ -351,7 +378,7 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
       cudaGraph_t g = nullptr;
       const uint64_t c0 = launches();
       if (cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2v, maxit);
+        for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2v, maxit, which);
         count_active(B, st.active, h->cnt.as<int>(), h->s);
         if (cudaStreamEndCapture(h->s, &g) == cudaSuccess && g) {
           if (cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
@@ -364,14 +391,26 @@ static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int ma
       if (exec) h->graphs[key] = std::make_pair(exec, nodes);
     }
   }
+  if (exec) {
+    CD_CUDA_OK(cudaGraphLaunch(exec, h->s));
+    count_launch((int)nodes);
+  } else {
+    for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2v, maxit, which);
+    count_active(B, st.active, h->cnt.as<int>(), h->s);
+  }
+  return CD_OK;
+}
+
+// Runs PCG on the workspace of precision T: r holds the right-hand side on entry, x the
+// solution on exit (x_0 = 0).  outer_active masks the solves that take part.
+template <typename T>
+static cd_status run_pcg(cd_solver h, int B, int pc, const double* tol2v, int maxit,
+                         const int* outer_active) {
+  const int flexible = pcg_begin<T>(h, B, pc, outer_active, 0);
+  const int chunk = std::max(1, h->opt.chunk);
   for (int done = 0; done < maxit + chunk; done += chunk) {
-    if (exec) {
-      CD_CUDA_OK(cudaGraphLaunch(exec, h->s));
-      count_launch((int)nodes);
-    } else {
-      for (int k = 0; k < chunk; ++k) pcg_iteration<T>(h, B, pc, flexible, tol2v, maxit);
-      count_active(B, st.active, h->cnt.as<int>(), h->s);
-    }
+    cd_status st = pcg_chunk<T>(h, B, pc, flexible, tol2v, maxit, 0);
+    if (st != CD_OK) return st;
     CD_CUDA_OK(cudaMemcpyAsync(h->h_cnt, h->cnt.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
     CD_CUDA_OK(cudaStreamSynchronize(h->s));
     if (*h->h_cnt == 0) break;
@@ -721,6 +760,295 @@ size_t solver_bytes(int d, int p, int n, const cd_options& opt) {
 }  // namespace cd
 
 // ====================================================================== C ABI
+namespace cd {
+// ---------------------------------------------------------------- serving sessions
+// Iteration-level continuous batching on one handle: each of the handle's max_batch slots runs
+// the refinement loop of solve_device on its own schedule (outer residual and check; an inner
+// FP32 or FP64 PCG solve advanced one chunk of iterations per step; the update), so a slot can
+// be given a new right-hand side between two chunks while the others keep iterating.  Every
+// kernel is masked per slot and every reduction has a fixed order per slot, so a slot's result
+// does not depend on what the other slots do.
+enum { SP_FREE = 0, SP_NEW = 1, SP_OUTER = 2, SP_IN32 = 3, SP_IN64 = 4, SP_DONE = 5 };
+
+// refinement-loop state of the masked slots at the start of their solve
+__global__ void sess_init_kernel(int B, const int* __restrict__ mask, int* active, int* status,
+                                 int* outer, int* inner) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !mask[b]) return;
+  active[b] = 1;
+  status[b] = CD_NOT_CONVERGED;
+  outer[b] = 0;
+  inner[b] = 0;
+}
+// out[b] = sum of the nb partials of solve b, for the masked solves (fixed order)
+__global__ void sum_partials_masked_kernel(const double* __restrict__ part, int nb, int B,
+                                           double* __restrict__ out, const int* __restrict__ mask) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !mask[b]) return;
+  double s = 0.0;
+  for (int i = 0; i < nb; ++i) s += part[(size_t)b * nb + i];
+  out[b] = s;
+}
+
+static cd_status sess_alloc(cd_solver h) {
+  const int B = h->Bcap;
+  if (!h->s_b.p) {
+    if (h->s_b.alloc(8 * (size_t)B * h->N) != cudaSuccess || h->s_x.alloc(8 * (size_t)B * h->N) != cudaSuccess ||
+        h->s_mask.alloc(4 * (size_t)B * 4) != cudaSuccess) {
+      cudaGetLastError();
+      return CD_ENOMEM;
+    }
+    // no PCG of either state is running
+    CD_CUDA_OK(cudaMemsetAsync(h->si[0].p, 0, 4 * (size_t)B, h->s));
+    CD_CUDA_OK(cudaMemsetAsync(h->si2[0].p, 0, 4 * (size_t)B, h->s));
+    h->sp.assign(B, SP_FREE);
+    h->s_alpha.assign(B, 1.0);
+    h->s_beta.assign(B, 1.0);
+    h->s_t0.resize(B);
+    h->h_mask.assign(4 * B, 0);
+  }
+  return CD_OK;
+}
+
+int sess_busy(cd_solver h) {
+  std::lock_guard<std::mutex> lk(h->mu);
+  int n = 0;
+  for (int v : h->sp) n += v != SP_FREE;
+  return n;
+}
+
+// Takes a free slot for right-hand side b (host, N doubles); it starts at the next step.
+cd_status sess_admit(cd_solver h, const double* b_host, double alpha, double beta, int* slot) {
+  if (!(alpha > 0) || !(beta > 0) || !std::isfinite(alpha) || !std::isfinite(beta)) return CD_EINVAL;
+  std::lock_guard<std::mutex> lk(h->mu);
+  cd_status st = sess_alloc(h);
+  if (st != CD_OK) return st;
+  int k = -1;
+  for (int i = 0; i < h->Bcap && k < 0; ++i)
+    if (h->sp[i] == SP_FREE) k = i;
+  if (k < 0) return CD_ENOMEM;
+  CD_CUDA_OK(cudaMemcpyAsync(h->s_b.as<double>() + (size_t)k * h->N, b_host, 8 * (size_t)h->N,
+                             cudaMemcpyHostToDevice, h->s));
+  h->s_alpha[k] = alpha;
+  h->s_beta[k] = beta;
+  h->sp[k] = SP_NEW;
+  h->s_t0[k] = std::chrono::steady_clock::now();
+  *slot = k;
+  return CD_OK;
+}
+
+// uploads mask j: the slots whose phase is `phase`
+static cd_status sess_mask(cd_solver h, int phase, int j) {
+  const int B = h->Bcap;
+  for (int b = 0; b < B; ++b) h->h_mask[j * B + b] = h->sp[b] == phase;
+  CD_CUDA_OK(cudaMemcpyAsync(h->s_mask.as<int>() + j * B, h->h_mask.data() + j * B, 4 * B,
+                             cudaMemcpyHostToDevice, h->s));
+  return CD_OK;
+}
+
+// One step of every occupied slot; `finished` receives the slots whose solve ended.
+cd_status sess_step(cd_solver h, std::vector<int>& finished) {
+  finished.clear();
+  std::lock_guard<std::mutex> lk(h->mu);
+  cd_status st = sess_alloc(h);
+  if (st != CD_OK) return st;
+  const int B = h->Bcap;
+  const long long N = h->N;
+  const int pc = h->opt.precond;
+  const bool ext = h->opt.ext_residual != 0;
+  const bool emu = ext && h->opt.emulated_fp64 && h->d == 2 && h->opt.precision != CD_PREC_FP64;
+  double* b = h->s_b.as<double>();
+  double* x = h->s_x.as<double>();
+  double* xlo = ext ? h->xlo64.as<double>() : nullptr;
+  int* mk[4];
+  for (int j = 0; j < 4; ++j) mk[j] = h->s_mask.as<int>() + j * B;
+  // 1. admissions: parameters (per-solve multigrid data of the new slots), initial state
+  std::vector<int> fresh;
+  for (int i = 0; i < B; ++i)
+    if (h->sp[i] == SP_NEW) fresh.push_back(i);
+  if (!fresh.empty()) {
+    CD_CUDA_OK(cudaMemcpyAsync(h->alpha.p, h->s_alpha.data(), 8 * B, cudaMemcpyHostToDevice, h->s));
+    CD_CUDA_OK(cudaMemcpyAsync(h->beta.p, h->s_beta.data(), 8 * B, cudaMemcpyHostToDevice, h->s));
+    h->dev_alpha = h->s_alpha;
+    h->dev_beta = h->s_beta;
+    for (MgData* mg : {&h->mg, &h->mgD}) {
+      const bool used = mg == &h->mg ? (pc == CD_PC_MG || pc == CD_PC_MIM) : (pc == CD_PC_WL && h->have_mgD);
+      if (!used) continue;
+      if ((st = mg_set_params_slots(*mg, h->d, h->P, h->s_alpha, h->s_beta, fresh, h->s)) != CD_OK)
+        return st;
+      if ((st = mg_prepare(*mg, B, coef_of(h), h->w64.apply_scratch.as<double>(), h->s)) != CD_OK)
+        return st;
+    }
+    // the batched solver's record of prepared parameters no longer holds
+    h->mg_alpha.clear();
+    h->mgD_alpha.clear();
+    std::vector<int> grp(B);
+    CD_CUDA_OK(cudaMemcpyAsync(grp.data(), h->ir_grp.p, 4 * B, cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaStreamSynchronize(h->s));
+    for (int i : fresh) {
+      const double ratio = std::max(h->s_alpha[i], h->s_beta[i]) / std::min(h->s_alpha[i], h->s_beta[i]);
+      grp[i] = (h->opt.precision == CD_PREC_FP32_IR && ratio < h->opt.mixed_switch_ratio) ? 0 : 2;
+    }
+    CD_CUDA_OK(cudaMemcpyAsync(h->ir_grp.p, grp.data(), 4 * B, cudaMemcpyHostToDevice, h->s));
+    if ((st = sess_mask(h, SP_NEW, 0)) != CD_OK) return st;
+    sess_init_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, mk[0], h->ir_active.as<int>(),
+                                                        h->ir_status.as<int>(), h->ir_outer.as<int>(),
+                                                        h->ir_inner_total.as<int>());
+    count_launch();
+    vzero<double>(N, B, x, mk[0], h->s);
+    if (ext) vzero<double>(N, B, xlo, mk[0], h->s);
+    const int nb = partial_blocks(N);
+    launch_dot<double>(b, b, N, B, h->part[1].as<double>(), nb, mk[0], h->s);
+    sum_partials_masked_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(h->part[1].as<double>(), nb, B,
+                                                                  h->ir_bnorm2.as<double>(), mk[0]);
+    count_launch();
+    CD_CUDA_OK(cudaStreamSynchronize(h->s));  // grp (host) goes out of scope
+    for (int i : fresh) h->sp[i] = SP_OUTER;
+  }
+  // 2. outer residual and check of the slots due for it; their inner solves start
+  if (std::count(h->sp.begin(), h->sp.end(), (int)SP_OUTER)) {
+    if ((st = sess_mask(h, SP_OUTER, 0)) != CD_OK) return st;
+    int npart = 0;
+    if ((st = outer_residual(h, B, b, x, xlo, mk[0], &npart)) != CD_OK) return st;
+    ir_check(B, h->part[0].as<double>(), npart, h->ir_bnorm2.as<double>(), h->ir_rnorm.as<double>(),
+             h->ir_rrprev.as<double>(), mk[0], h->ir_status.as<int>(), h->ir_relres.as<double>(),
+             h->ir_outer.as<int>(), h->ir_grp.as<int>(), h->ir_tol2.as<double>(),
+             h->opt.rtol * h->opt.rtol, h->opt.inner_rtol * h->opt.inner_rtol, h->opt.max_outer,
+             h->ir_inner_total.as<int>(), h->opt.maxit, emu ? 1e-12 : 1e-30, h->s);
+    std::vector<int> still(B), grp(B);
+    CD_CUDA_OK(cudaMemcpyAsync(still.data(), mk[0], 4 * B, cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaMemcpyAsync(grp.data(), h->ir_grp.p, 4 * B, cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaStreamSynchronize(h->s));
+    // masks 1 / 2: the slots that start an FP32 / FP64 inner solve now
+    bool any32 = false, any64 = false;
+    for (int i = 0; i < B; ++i) {
+      const bool go = h->sp[i] == SP_OUTER && still[i];
+      h->h_mask[1 * B + i] = go && grp[i] == 0;
+      h->h_mask[2 * B + i] = go && grp[i] != 0;
+      any32 |= h->h_mask[1 * B + i] != 0;
+      any64 |= h->h_mask[2 * B + i] != 0;
+      if (h->sp[i] == SP_OUTER && !still[i]) {
+        h->sp[i] = SP_DONE;
+        finished.push_back(i);
+      }
+    }
+    CD_CUDA_OK(cudaMemcpyAsync(mk[1], h->h_mask.data() + B, 8 * B, cudaMemcpyHostToDevice, h->s));
+    if (any32) {
+      ir_cast(N, B, h->r64.as<double>(), h->w32.r.as<float>(), h->ir_rnorm.as<double>(), mk[1], h->s);
+      pcg_begin<float>(h, B, pc, mk[1], 0, 1);
+    }
+    if (any64) {
+      scale_div(N, B, h->r64.as<double>(), h->w64.r.as<double>(), h->ir_rnorm.as<double>(), mk[2], h->s);
+      set_fp64_emulated(emu ? 1 : 0);
+      g_lowp_prec = h->opt.precision == CD_PREC_FP32_IR ? 1 : 0;
+      pcg_begin<double>(h, B, pc, mk[2], 1, 1);
+      set_fp64_emulated(0);
+      g_lowp_prec = 0;
+    }
+    for (int i = 0; i < B; ++i)
+      if (h->sp[i] == SP_OUTER) h->sp[i] = h->h_mask[1 * B + i] ? SP_IN32 : SP_IN64;
+  }
+  // 3. one chunk of each inner group, then the slots whose inner solve ended take their update
+  const bool run32 = std::count(h->sp.begin(), h->sp.end(), (int)SP_IN32) > 0;
+  const bool run64 = std::count(h->sp.begin(), h->sp.end(), (int)SP_IN64) > 0;
+  const bool fd = pc == CD_PC_FD_D || pc == CD_PC_FD_T;
+  const bool mgk = pc == CD_PC_MG || pc == CD_PC_MIM || pc == CD_PC_WL;
+  const int flex32 = (mgk || (h->opt.fd_tensor_cores && fd)) ? 1 : 0;
+  const int flex64 = (mgk || (h->opt.precision == CD_PREC_FP32_IR && fd)) ? 1 : 0;
+  if (run32 &&
+      (st = pcg_chunk<float>(h, B, pc, flex32, h->ir_tol2.as<double>(), h->opt.inner_maxit, 0)) != CD_OK)
+    return st;
+  if (run64) {
+    set_fp64_emulated(emu ? 1 : 0);
+    g_lowp_prec = h->opt.precision == CD_PREC_FP32_IR ? 1 : 0;
+    st = pcg_chunk<double>(h, B, pc, flex64, h->ir_tol2.as<double>(), h->opt.maxit, 1);
+    set_fp64_emulated(0);
+    g_lowp_prec = 0;
+    if (st != CD_OK) return st;
+  }
+  if (run32 || run64) {
+    std::vector<int> a32(B), a64(B);
+    CD_CUDA_OK(cudaMemcpyAsync(a32.data(), h->si[0].p, 4 * B, cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaMemcpyAsync(a64.data(), h->si2[0].p, 4 * B, cudaMemcpyDeviceToHost, h->s));
+    CD_CUDA_OK(cudaStreamSynchronize(h->s));
+    bool e32 = false, e64 = false;
+    for (int i = 0; i < B; ++i) {
+      h->h_mask[1 * B + i] = h->sp[i] == SP_IN32 && !a32[i];
+      h->h_mask[2 * B + i] = h->sp[i] == SP_IN64 && !a64[i];
+      e32 |= h->h_mask[1 * B + i] != 0;
+      e64 |= h->h_mask[2 * B + i] != 0;
+    }
+    CD_CUDA_OK(cudaMemcpyAsync(mk[1], h->h_mask.data() + B, 8 * B, cudaMemcpyHostToDevice, h->s));
+    if (e32) {
+      add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si[1].as<int>(), mk[1],
+                                                          h->ir_inner_total.as<int>());
+      count_launch();
+      if (ext)
+        launch_ext_update<float>(N, B, x, xlo, h->w32.x.as<float>(), h->ir_rnorm.as<double>(), mk[1], h->s);
+      else
+        ir_update(N, B, x, h->w32.x.as<float>(), h->ir_rnorm.as<double>(), mk[1], h->s);
+    }
+    if (e64) {
+      add_iters_kernel<<<(B + 127) / 128, 128, 0, h->s>>>(B, h->si2[1].as<int>(), mk[2],
+                                                          h->ir_inner_total.as<int>());
+      count_launch();
+      if (ext)
+        launch_ext_update<double>(N, B, x, xlo, h->w64.x.as<double>(), h->ir_rnorm.as<double>(), mk[2], h->s);
+      else
+        ir_update64(N, B, x, h->w64.x.as<double>(), h->ir_rnorm.as<double>(), mk[2], h->s);
+    }
+    for (int i = 0; i < B; ++i)
+      if (h->h_mask[1 * B + i] || h->h_mask[2 * B + i]) h->sp[i] = SP_OUTER;
+  }
+  CD_CUDA_OK(cudaGetLastError());
+  return CD_OK;
+}
+
+// The result of a finished slot: its solution x (FP64; with the double-FP64 residual the
+// rounding of x + x_lo) into x_host, its cd_result (residual of that x); frees the slot.
+cd_status sess_take(cd_solver h, int slot, double* x_host, cd_result* res) {
+  std::lock_guard<std::mutex> lk(h->mu);
+  if (slot < 0 || slot >= (int)h->sp.size() || h->sp[slot] != SP_DONE) return CD_EINVAL;
+  const int B = h->Bcap;
+  const long long N = h->N;
+  for (int i = 0; i < B; ++i) h->h_mask[3 * B + i] = i == slot;
+  int* mk3 = h->s_mask.as<int>() + 3 * B;
+  CD_CUDA_OK(cudaMemcpyAsync(mk3, h->h_mask.data() + 3 * B, 4 * B, cudaMemcpyHostToDevice, h->s));
+  int npart = 0;
+  cd_status st = outer_residual(h, B, h->s_b.as<double>(), h->s_x.as<double>(), nullptr, mk3, &npart);
+  if (st != CD_OK) return st;
+  const int nb = partial_blocks(N);
+  launch_dot<double>(h->s_b.as<double>(), h->s_b.as<double>(), N, B, h->part[1].as<double>(), nb, mk3, h->s);
+  std::vector<double> prr(npart), pbb(nb);
+  int status = 0, outer = 0, inner = 0;
+  CD_CUDA_OK(cudaMemcpyAsync(prr.data(), h->part[0].as<double>() + (size_t)slot * npart, 8 * npart,
+                             cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(pbb.data(), h->part[1].as<double>() + (size_t)slot * nb, 8 * nb,
+                             cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(&status, h->ir_status.as<int>() + slot, 4, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(&outer, h->ir_outer.as<int>() + slot, 4, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(&inner, h->ir_inner_total.as<int>() + slot, 4, cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaMemcpyAsync(x_host, h->s_x.as<double>() + (size_t)slot * N, 8 * (size_t)N,
+                             cudaMemcpyDeviceToHost, h->s));
+  CD_CUDA_OK(cudaStreamSynchronize(h->s));
+  double rr = 0, bb = 0;
+  for (double v : prr) rr += v;
+  for (double v : pbb) bb += v;
+  const double rel = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  if (status == CD_OK && !(rel <= h->opt.rtol)) status = CD_NOT_CONVERGED;
+  if (res) {
+    res->iters_outer = outer;
+    res->iters_inner = inner;
+    res->relres = rel;
+    res->relres_hi = rel;
+    res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - h->s_t0[slot]).count();
+    res->status = status;
+  }
+  h->sp[slot] = SP_FREE;
+  return CD_OK;
+}
+}  // namespace cd
+
 extern "C" {
 
 void cd_default_options(cd_options* o) {
@@ -781,6 +1109,8 @@ static bool alloc_workspace(cd_solver h, long long scratch_elems) {
   bool ok = al(h->alpha, 8 * B) && al(h->beta, 8 * B);
   for (auto& x : h->sd) ok = ok && al(x, 8 * B);
   for (auto& x : h->si) ok = ok && al(x, 4 * B);
+  for (auto& x : h->sd2) ok = ok && al(x, 8 * B);
+  for (auto& x : h->si2) ok = ok && al(x, 4 * B);
   for (auto& x : h->part) ok = ok && al(x, 8 * (size_t)B * kMaxPartials);
   ok = ok && al(h->ir_rnorm, 8 * B) && al(h->ir_bnorm2, 8 * B) && al(h->ir_relres, 8 * B) &&
        al(h->ir_active, 4 * B) && al(h->ir_status, 4 * B) && al(h->ir_outer, 4 * B) &&
@@ -949,7 +1279,9 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     const std::string v64s = v64 ? v64 : "";
     set_apply_fp64_variant(v64s == "v3" ? 1 : v64s == "ff" ? 2 : v64s == "ff2" ? 3 : v64s == "ff1" ? 4 : 0);
     const char* v3d = std::getenv("CURLDIV_APPLY3D_KERNEL");
-    set_apply3d_variant(v3d && std::string(v3d) == "multipass" ? 0 : 1);
+    const std::string v3ds = v3d ? v3d : "";
+    set_apply3d_variant(v3ds == "multipass" ? 0 : v3ds == "axis" ? 2 : v3ds == "stream" ? 3
+                        : v3ds == "pass64" ? 4 : 1);
   }
   if (h->opt.precond == CD_PC_FD_D || h->opt.precond == CD_PC_FD_T) {
     cd_status st = ensure_fd(h.get());

@@ -61,3 +61,24 @@ def test_emulated_inner_solves_reach_rtol_like_fp64(p, n):
     print("inner iterations emulated / FP64:", out[1], out[0])
     for k in range(B):
         assert out[1][k] <= 1.6 * out[0][k] + 20, (k, out)
+
+
+@pytest.mark.parametrize("p,n,beta", [(1, 7, 1.0), (2, 9, 1e-6), (3, 11, 1e3), (5, 6, 1e6)])
+def test_double_fp32_3d_apply_matches_oracle(p, n, beta, monkeypatch):
+    """The 3D apply in double-FP32 (the three tuned passes with (hi, lo) FP32 intermediates),
+    elementwise against the oracle's assembled matrix."""
+    monkeypatch.setenv("CURLDIV_APPLY_KERNEL_FP64", "ff")
+    d, B = 3, 2
+    W = inputs.uniform_rhs(d, p, n, seed=33, nrhs=B)
+    s = cdl.Solver(d, p, n, 1.0, beta, max_batch=B, autotune=0)
+    w = torch.as_tensor(W.ravel(), device="cuda")
+    y = torch.zeros_like(w)
+    s.cd_apply(w, y)
+    Y = y.cpu().numpy().reshape(B, -1)
+    A = oracle_matrix(d, p, n, 1.0, beta)
+    worst = 0.0
+    for k in range(B):
+        err = np.abs(Y[k] - A @ W[k]) / abs_matvec_bound(A, W[k])
+        worst = max(worst, float(err.max()))
+    print("double-FP32 3D apply, worst error / (|A||w|):", p, n, beta, worst)
+    assert worst <= FF_TOL, worst

@@ -39,11 +39,13 @@ APPLY_CASES = [(2, 1, 9), (2, 2, 16), (2, 3, 37), (2, 5, 30), (2, 2, 3), (2, 6, 
 @pytest.mark.parametrize("d,p,n", APPLY_CASES)
 def test_apply_fp64_and_fp32_match_oracle(d, p, n, variant, monkeypatch):
     """Every 2D kernel (FP32: v5 folded tiles, v3 packed pairs; v2; plain shared-memory v1) and
-    both 3D kernels (streaming default, three banded passes) against the oracle."""
-    if d == 3 and variant in ("v1", "v5"):
-        pytest.skip("two 3D kernels")
+    the 3D designs (streaming, the tuned three passes in FP32 and FP64, the generic axis passes)
+    against the oracle."""
+    if d == 3 and variant == "v5":
+        pytest.skip("three 3D designs")
     if d == 3:
-        monkeypatch.setenv("CURLDIV_APPLY3D_KERNEL", "stream" if variant == "v3" else "multipass")
+        monkeypatch.setenv("CURLDIV_APPLY3D_KERNEL",
+                           {"v3": "stream", "v2": "pass64", "v1": "axis"}[variant])
     else:
         monkeypatch.setenv("CURLDIV_APPLY_KERNEL", variant)
         monkeypatch.setenv("CURLDIV_APPLY_KERNEL_FP64", "v3" if variant == "v3" else "v2")

@@ -1,4 +1,5 @@
-"""GPU tests of the serving runtime (continuous batching, admission, cancellation, timeouts)."""
+"""GPU tests of the serving runtime (iteration-level continuous batching, admission,
+cancellation, timeouts)."""
 import time
 
 import numpy as np
@@ -36,7 +37,7 @@ def test_results_are_the_same_alone_and_in_the_mix():
     st = srv.stats()
     srv.close()
     assert st["completed"] == len(reqs) and st["failed"] == 0
-    assert st["batches"] < len(reqs)  # same-shape requests were batched together
+    assert st["mean_batch"] > 1.0  # same-shape solves shared the session steps
     for (d, p, n, al, be, b), (status, x, res) in zip(reqs, outs):
         assert status == cdl.CD_OK
         nrhs = len(al)
@@ -88,3 +89,28 @@ def test_cancel_timeout_and_invalid_requests():
     srv.close()
     sts = [o[0] for o in outs]
     assert cdl.CD_TIMEOUT in sts and all(s in (cdl.CD_OK, cdl.CD_TIMEOUT) for s in sts)
+
+
+def test_requests_join_and_leave_between_krylov_chunks():
+    """A request submitted while a long solve of the same shape is running is admitted into a
+    free slot of the running session and finishes first (it does not wait for the long solve),
+    and both results equal those of the same solves alone."""
+    d, p, n = 2, 3, 40
+    b_long = inputs.uniform_rhs(d, p, n, seed=41).ravel()
+    b_short = inputs.uniform_rhs(d, p, n, seed=42).ravel()
+    srv = cdl.Server(workers=1, max_batch=4, solve=SOLVE)
+    t_long = srv.submit(d, p, n, [1.0], [1e6], b_long)  # thousands of FP64-group iterations
+    time.sleep(0.5)  # the long solve is on the GPU
+    t_short = srv.submit(d, p, n, [1.0], [1.0], b_short)  # a few dozen iterations
+    out_short = srv.wait(t_short)
+    assert srv.poll(t_long) is None  # still running when the short one is done
+    out_long = srv.wait(t_long)
+    srv.close()
+    for (st, x, res), b, beta in ((out_short, b_short, 1.0), (out_long, b_long, 1e6)):
+        assert st == cdl.CD_OK, res
+        s = cdl.Solver(d, p, n, max_batch=4, **SOLVE)
+        x1 = np.zeros_like(b)
+        st1, res1 = s.cd_solve_host(b.copy(), x1, [1.0], [beta])
+        assert st1 == cdl.CD_OK
+        np.testing.assert_array_equal(x, x1)
+        assert res[0]["iters_inner"] == res1[0]["iters_inner"]
