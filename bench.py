@@ -729,7 +729,8 @@ def run_profile_kernel(args):
     on the tensor cores at the same size (four passes each); `tail` = the kind of iteration that
     dominates a sweep step: 16 solves at beta/alpha = 1e-6 and 1e6 (p = 3, n = 256, mixed
     precision, which runs them in the FP64 inner group), multigrid FCG capped at 120 iterations;
-    `ff` = the double-FP32 2D apply of those inner solves at p = 3, n = 256, batch 16."""
+    `ff` = the double-FP32 2D apply of those inner solves at p = 3, n = 256, batch 16; `ff3d` =
+    the double-FP32 3D passes at p = 3, n = 64, batch 4."""
     import torch
     from paper_1805_10058_gb300 import curldiv as cdl
     B = 40
@@ -749,6 +750,14 @@ def run_profile_kernel(args):
         w = torch.rand(B * s.N, dtype=torch.float64, device="cuda")
         y = torch.empty_like(w)
         for _ in range(4):
+            s.cd_apply(w, y, [1.0] * B, [1e6] * B)
+    elif args.profile_kernel == "ff3d":
+        os.environ["CURLDIV_APPLY_KERNEL_FP64"] = "ff"
+        B = 4
+        s = cdl.Solver(3, 3, 64, max_batch=B, precond=cdl.CD_PC_NONE, autotune=0)
+        w = torch.rand(B * s.N, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(w)
+        for _ in range(3):
             s.cd_apply(w, y, [1.0] * B, [1e6] * B)
     elif args.profile_kernel == "apply":
         s = cdl.Solver(2, 3, N_INT, max_batch=B, precond=cdl.CD_PC_NONE, autotune=0)
@@ -785,7 +794,7 @@ def main():
     ap.add_argument("--serving", action="store_true", help="serving-stream workload instead")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--workers", type=int, default=4)
-    ap.add_argument("--profile-kernel", choices=["apply", "fd", "tail", "ff"], default=None,
+    ap.add_argument("--profile-kernel", choices=["apply", "fd", "tail", "ff", "ff3d"], default=None,
                     help="a few launches of one kernel for ncu, no timing")
     args = ap.parse_args()
     if args.profile_kernel:

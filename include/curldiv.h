@@ -129,7 +129,7 @@ typedef struct {
                           and n = 256 an FP64 evaluation bottoms out near 1e-8).  0: FP64
                           solution and residual.                                           */
   int emulated_fp64;   /* 1 (default, with ext_residual and CD_PREC_FP32_IR): the FP64 inner
-                          Krylov solves of 2D problems apply the operator in double-FP32 (about 48
+                          Krylov solves (2D and 3D) apply the operator in double-FP32 (about 48
                           significant bits) on the FP32 pipe, several times the FP64 rate on
                           GB300; their inner tolerance is then floored at 1e-6 relative and the
                           double-FP64 outer residual restores the accuracy.  0: FP64 applies.  */
@@ -309,7 +309,11 @@ CD_API uint64_t cd_kernel_launches(void);
  * fits in `hbm_budget`, evicting idle solvers (least recently used) when needed.  A request's
  * results do not depend on what else runs (every kernel is masked per slot and every
  * reduction has a fixed order per slot): they equal those of cd_solve_host on the same
- * right-hand side.  Host buffers only; the server copies b at submit and x at poll/wait. */
+ * right-hand side with half the tolerance.  The server returns the FP64 vector x, whose
+ * residual exceeds that of the refinement's x + x_lo by the rounding of x (about
+ * eps |A| |x|, a sizeable part of 1e-10 at beta/alpha near 1e+-6): the sessions refine to
+ * solve.rtol / 2 and a right-hand side's status is CD_OK iff the returned x has relres <=
+ * solve.rtol.  Host buffers only; the server copies b at submit and x at poll/wait. */
 typedef struct cd_server_s* cd_server;
 
 typedef struct {

@@ -13,8 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcurldiv.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["setup.cpp", "kernels.cu", "krylov.cu", "mg.cu", "solver.cu", "server.cpp",
-           "static_apply.cu", "fd_tc.cu", "ext_residual.cu", "ksmooth.cu", "spectral.cu"]
+SOURCES = ["setup.cpp", "kernels.cu", "apply2d_ff.cu", "apply3d_pass.cu", "krylov.cu", "mg.cu",
+           "solver.cu", "server.cpp", "static_apply.cu", "fd_tc.cu", "ext_residual.cu", "ksmooth.cu",
+           "spectral.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -125,6 +125,9 @@ void set_apply_variant(int v);
 // 3D apply: 1 = streaming fused kernel (default), 0 = three banded passes (kept for checks).
 void set_apply3d_variant(int v);
 void set_apply_fp64_variant(int v);  // 2D FP64: 0 = v2, 1 = v3, 2 = double-FP32 everywhere
+// double-FP32 2D apply tile rows: 0 = chosen by the grid size, 8 = narrow tile, else wide tile
+void set_ff2_rows(int rows);
+int num_sms();  // SMs of the current device (cached after the first call)
 // The calling thread's FP64 2D applies (modes 0 and 1) run in double-FP32 arithmetic on the
 // FP32 pipe while set (the inner FP64 Krylov solves of the refinement loop); fp64_emulated()
 // tells whether they do now.

@@ -39,4 +39,34 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)d);
 }
 
+// FP64 -> (hi, lo) by conversions (host-side constants and per-CTA scalars)
+__device__ __forceinline__ float2 ff_split(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(__dsub_rn(v, (double)h)));
+}
+// acc += c * x (all double-FP32)
+__device__ __forceinline__ void ff_fma(float2& acc, float2 c, float2 x) {
+  const float p = __fmul_rn(c.x, x.x);
+  float e = __fmaf_rn(c.x, x.x, -p);
+  e = __fmaf_rn(c.x, x.y, e);
+  e = __fmaf_rn(c.y, x.x, e);
+  const float sm = __fadd_rn(acc.x, p);
+  const float bb = __fsub_rn(sm, acc.x);
+  const float er = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(sm, bb)), __fsub_rn(p, bb));
+  acc.y = __fadd_rn(acc.y, __fadd_rn(er, e));
+  acc.x = sm;
+}
+__device__ __forceinline__ float2 ff_norm(float2 a) {
+  const float sm = __fadd_rn(a.x, a.y);
+  return make_float2(sm, __fsub_rn(a.y, __fsub_rn(sm, a.x)));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  float2 acc = make_float2(0.f, 0.f);
+  ff_fma(acc, a, b);
+  return ff_norm(acc);
+}
+__device__ __forceinline__ double ff_to_double(float2 a) {
+  return __dadd_rn(f2d_bits(a.x), f2d_bits(a.y));
+}
+
 }  // namespace cd

@@ -23,6 +23,7 @@
 #include <unordered_map>
 
 #include "cd_internal.h"
+#include "apply_shared.h"
 #include "ffmath.h"
 
 namespace cd {
@@ -30,69 +31,7 @@ namespace cd {
 static int g_use_stream3d = 1;  // 3D: 1 = streaming fused kernel, 0 = three banded passes
 
 // ------------------------------------------------------------------ helpers
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
-// Block-wide sum of a double (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
-__device__ double block_sum(double v) {
-  __shared__ double red[32];
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (wid == 0) {
-    s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
-    s = warp_sum(s);
-  }
-  return s;
-}
-
-// Chebyshev step coefficients of one solve: d = c1 dprev + c2 D^{-1} r (c1 = 0 for step 0).
-__device__ __forceinline__ void cheb_coef(double lmax, int step, double& c1, double& c2) {
-  const double hi = kChebHi * lmax, lo = hi / kChebRatio;
-  const double th = 0.5 * (hi + lo), de = 0.5 * (hi - lo), sigma = th / de;
-  if (step == 0) {
-    c1 = 0.0;
-    c2 = 1.0 / th;
-    return;
-  }
-  double rho_prev = 1.0 / sigma, rho = rho_prev;
-  for (int j = 1; j <= step; ++j) {
-    rho_prev = rho;
-    rho = 1.0 / (2.0 * sigma - rho_prev);
-  }
-  c1 = rho * rho_prev;
-  c2 = 2.0 * rho / de;
-}
-
-// The same coefficients computed once per CTA (thread 0, FP64) and shared.  GB300's FP64 pipe
-// runs at 1/64 of the FP32 rate, so a per-thread FP64 recurrence with divisions costs more than
-// a whole FP32 stencil.  Every thread of the CTA must reach this call.
-__device__ __forceinline__ void cheb_coef_cta(double lmax, int step, double& c1, double& c2) {
-  __shared__ double s_cc[2];
-  if (threadIdx.x == 0) {
-    double a, b;
-    cheb_coef(lmax, step, a, b);
-    s_cc[0] = a;
-    s_cc[1] = b;
-  }
-  __syncthreads();
-  c1 = s_cc[0];
-  c2 = s_cc[1];
-}
-
-template <typename T>
-__device__ __forceinline__ void cheb_epi(const Epi<T>& e, long long o, T r, T dinv, T c1, T c2) {
-  T d = c2 * dinv * r;
-  if (e.step > 0) d += c1 * e.dprev[o];
-  e.xout[o] = e.xprev[o] + d;
-  if (e.dout) e.dout[o] = d;
-  if (e.rout) e.rout[o] = r;
-}
 
 // 1 / (x * y * z + u * v * t) rounded step by step (no contraction), shared by every 2D kernel's
 // fused smoother epilogue so that all of them produce the same bits.
@@ -540,11 +479,6 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) apply2d_v3_kernel
 }
 
 // ---- stencil registry: band device pointer -> central stencil of that level (host copy)
-struct StencilHost {
-  int m, P, lo, hi;
-  double c[3][13];
-  float2* ffT;  // device: the level's k-major bands [3][2P+1][m] split into (hi, lo) FP32 pairs
-};
 static std::mutex g_stencil_mu;
 static std::unordered_map<const void*, StencilHost> g_stencils;
 
@@ -592,7 +526,7 @@ void unregister_level(const void* bands_dev) {
     g_stencils.erase(it);
   }
 }
-static bool find_level(const void* bands_dev, StencilHost& out) {
+bool find_level(const void* bands_dev, StencilHost& out) {
   std::lock_guard<std::mutex> lk(g_stencil_mu);
   auto it = g_stencils.find(bands_dev);
   if (it == g_stencils.end()) return false;
@@ -1001,14 +935,6 @@ static void set_v5_attr() {
                        (int)V5Tile<P>::smem);
 }
 
-static bool stencil_folds(const StencilHost& sh) {
-  const int P = sh.P;
-  for (int t = 1; t <= P; ++t) {
-    if (sh.c[0][P - t] != sh.c[0][P + t] || sh.c[2][P - t] != sh.c[2][P + t]) return false;
-    if (sh.c[1][P - t] != -sh.c[1][P + t]) return false;
-  }
-  return sh.c[1][P] == 0.0;
-}
 
 template <int P>
 static bool launch_v5_P(int m, const float* bands, const StencilHost& sh, const float* w, float* y,
@@ -1741,6 +1667,18 @@ static int tuned_variant(size_t es, int m, int P, int /*B*/) {
   auto it = g_tuned.find(std::make_tuple((int)es, m, P));
   return it == g_tuned.end() ? 0 : it->second;
 }
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+    else
+      return 148;
+  }
+  return n;
+}
 static int g_use_v2 = 2;  // 2: v5 then v3 kernel (FP32), 3: v3 only, 1: v2 kernel, 0: v1 kernel
 void set_apply_variant(int v) { g_use_v2 = v; }
 static int g_fp64_v3 = 0;    // FP64 2D apply: 0 = v2 (default), 1 = v3 (8 rows per tile)
@@ -1764,647 +1702,9 @@ void set_apply3d_variant(int v) {
   g_use_pass3d = v == 2 ? 0 : v == 4 ? 2 : 1;
 }
 
-// ------------------------------------------------------------------ 2D apply in double-FP32
-// FP64 vectors, arithmetic in double-FP32 ("float-float": an unevaluated sum hi + lo of two FP32
-// numbers, about 48 significant bits) on the FP32 pipe, which on GB300 issues 64 times the FP64
-// rate.  Each FP64 input element of the tile is split once into (hi, lo) in shared memory; every
-// product is an FMA two-product with the cross terms, every sum a two-sum (non-contracting _rn
-// intrinsics); the x_2 results, scaled and grouped as in the FP32 kernel (PM, PS, PA), stay in
-// shared memory as (hi, lo) pairs, and the x_1 pass forms y in double-FP32 and rounds it to FP64.
-// Accuracy: about 1e-13 of (|A| |w|)_i, 30x coarser than FP64, used for the inner Krylov solves
-// of the refinement loop (whose double-FP64 outer residual removes it).
-struct StencilFF {
-  float2 c[3][13];
-  int lo, hi;
-};
-
-__device__ __forceinline__ float2 ff_split(double v) {
-  const float h = __double2float_rn(v);
-  return make_float2(h, __double2float_rn(__dsub_rn(v, (double)h)));
-}
-// acc += c * x (all double-FP32)
-__device__ __forceinline__ void ff_fma(float2& acc, float2 c, float2 x) {
-  const float p = __fmul_rn(c.x, x.x);
-  float e = __fmaf_rn(c.x, x.x, -p);
-  e = __fmaf_rn(c.x, x.y, e);
-  e = __fmaf_rn(c.y, x.x, e);
-  const float sm = __fadd_rn(acc.x, p);
-  const float bb = __fsub_rn(sm, acc.x);
-  const float er = __fadd_rn(__fsub_rn(acc.x, __fsub_rn(sm, bb)), __fsub_rn(p, bb));
-  acc.y = __fadd_rn(acc.y, __fadd_rn(er, e));
-  acc.x = sm;
-}
-__device__ __forceinline__ float2 ff_norm(float2 a) {
-  const float sm = __fadd_rn(a.x, a.y);
-  return make_float2(sm, __fsub_rn(a.y, __fsub_rn(sm, a.x)));
-}
-__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
-  float2 acc = make_float2(0.f, 0.f);
-  ff_fma(acc, a, b);
-  return ff_norm(acc);
-}
-__device__ __forceinline__ double ff_to_double(float2 a) {
-  return __dadd_rn(f2d_bits(a.x), f2d_bits(a.y));
-}
-
-template <int P, int TR>
-__global__ void __launch_bounds__(256, 2) apply2d_ff_kernel(
-    int m, const float2* __restrict__ bandF, StencilFF cs, const double* __restrict__ w,
-    double* __restrict__ y, const double* __restrict__ rhs, int mode,
-    const double* __restrict__ alpha, const double* __restrict__ beta,
-    const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
-    Epi<double> epi) {
-  constexpr int W = 2 * P + 1, TC = 64, HR = TR + 2 * P, HC = TC + 2 * P;
-  const int b = blockIdx.z;
-  if (active && !active[b]) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* sw = reinterpret_cast<float2*>(smem_raw);  // [2][HR][HC] input tile, (hi, lo)
-  float2* sp = sw + 2 * HR * HC;                      // [3][2][HR][TC] intermediates
-  const long long N = 2LL * m * m;
-  const double* wb = w + (long long)b * N;
-  const int c0 = blockIdx.x * TC, r0 = blockIdx.y * TR;
-  const float2 al = ff_split(alpha[b]), be = ff_split(beta[b]);
-  const float2 ga = ff_split((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
-  const float2* BM = bandF;
-  const float2* BA = bandF + (size_t)W * m;
-  const float2* BS = bandF + (size_t)2 * W * m;
-  // tile of w with halos, split once
-  for (int idx = threadIdx.x; idx < 2 * HR * HC; idx += blockDim.x) {
-    const int c = idx / (HR * HC), rem = idx - c * HR * HC;
-    const int rr = rem / HC, cc = rem - rr * HC;
-    const int row = r0 - P + rr, col = c0 - P + cc;
-    float2 v = make_float2(0.f, 0.f);
-    if (row >= 0 && row < m && col >= 0 && col < m)
-      v = ff_split_bits(wb[(long long)c * m * m + (long long)row * m + col]);
-    sw[idx] = v;
-  }
-  __syncthreads();
-  // axis x_2 for rows r0-P .. r0+TR+P-1: S2, M2, A2 of both components, scaled and grouped
-  for (int item = threadIdx.x; item < HR * TC; item += blockDim.x) {
-    const int q = item / TC, cc = item - q * TC;
-    const int row = r0 - P + q, j = c0 + cc;
-    float2 tM[2], tA[2], tS[2];
-    for (int c = 0; c < 2; ++c) tM[c] = tA[c] = tS[c] = make_float2(0.f, 0.f);
-    if (row >= 0 && row < m && j < m) {
-      const bool interior = j >= cs.lo && j < cs.hi;
-#pragma unroll
-      for (int k = 0; k < W; ++k) {
-        float2 cM, cA, cS;
-        if (interior) {
-          cM = cs.c[0][k];
-          cA = cs.c[1][k];
-          cS = cs.c[2][k];
-        } else {
-          cM = BM[(size_t)k * m + j];
-          cA = BA[(size_t)k * m + j];
-          cS = BS[(size_t)k * m + j];
-        }
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const float2 v = sw[(c * HR + q) * HC + cc + k];
-          ff_fma(tM[c], cM, v);
-          ff_fma(tA[c], cA, v);
-          ff_fma(tS[c], cS, v);
-        }
-      }
-      for (int c = 0; c < 2; ++c) {
-        tM[c] = ff_norm(tM[c]);
-        tA[c] = ff_norm(tA[c]);
-        tS[c] = ff_norm(tS[c]);
-      }
-    }
-    // PM = (alpha S2 w1, beta S2 w2) feeds M1; PS = (beta M2 w1, alpha M2 w2) feeds S1;
-    // PA = gamma (A2 w2, A2 w1) feeds A1
-    sp[((0 * 2 + 0) * HR + q) * TC + cc] = ff_mul(al, tS[0]);
-    sp[((0 * 2 + 1) * HR + q) * TC + cc] = ff_mul(be, tS[1]);
-    sp[((1 * 2 + 0) * HR + q) * TC + cc] = ff_mul(be, tM[0]);
-    sp[((1 * 2 + 1) * HR + q) * TC + cc] = ff_mul(al, tM[1]);
-    sp[((2 * 2 + 0) * HR + q) * TC + cc] = ff_mul(ga, tA[1]);
-    sp[((2 * 2 + 1) * HR + q) * TC + cc] = ff_mul(ga, tA[0]);
-  }
-  __syncthreads();
-  // axis x_1: y_c = M1 PM_c + S1 PS_c + A1 PA_c
-  double acc = 0.0, ec1 = 0.0, ec2 = 0.0;
-  if (mode == 2) cheb_coef_cta(epi.lmax[b], epi.step, ec1, ec2);
-  for (int item = threadIdx.x; item < TR * TC; item += blockDim.x) {
-    const int r = item / TC, cc = item - r * TC;
-    const int i = r0 + r, j = c0 + cc;
-    if (i >= m || j >= m) continue;
-    const bool interior = i >= cs.lo && i < cs.hi;
-    float2 yy[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-      float2 cM, cA, cS;
-      if (interior) {
-        cM = cs.c[0][k];
-        cA = cs.c[1][k];
-        cS = cs.c[2][k];
-      } else {
-        cM = BM[(size_t)k * m + i];
-        cA = BA[(size_t)k * m + i];
-        cS = BS[(size_t)k * m + i];
-      }
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        ff_fma(yy[c], cM, sp[((0 * 2 + c) * HR + r + k) * TC + cc]);
-        ff_fma(yy[c], cS, sp[((1 * 2 + c) * HR + r + k) * TC + cc]);
-        ff_fma(yy[c], cA, sp[((2 * 2 + c) * HR + r + k) * TC + cc]);
-      }
-    }
-    const long long o1 = (long long)b * N + (long long)i * m + j, o2 = o1 + (long long)m * m;
-    double y1 = ff_to_double(ff_norm(yy[0])), y2 = ff_to_double(ff_norm(yy[1]));
-    if (mode == 2) {  // fused Chebyshev step with the stored 1 / diag(A)
-      cheb_epi(epi, o1, rhs[o1] - y1, epi.dinv[o1], ec1, ec2);
-      cheb_epi(epi, o2, rhs[o2] - y2, epi.dinv[o2], ec1, ec2);
-      continue;
-    }
-    if (mode == 1) {
-      y1 = rhs[o1] - y1;
-      y2 = rhs[o2] - y2;
-      if (dotp) acc += y1 * y1 + y2 * y2;
-    } else if (dotp) {
-      acc += w[o1] * y1 + w[o2] * y2;
-    }
-    y[o1] = y1;
-    y[o2] = y2;
-  }
-  if (dotp) {
-    const double sum = block_sum(acc);
-    if (threadIdx.x == 0)
-      dotp[(size_t)b * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = sum;
-  }
-}
-
-template <int P, int TR>
-static size_t ff_smem() {
-  return sizeof(float2) * ((size_t)2 * (TR + 2 * P) * (64 + 2 * P) + (size_t)6 * (TR + 2 * P) * 64);
-}
-template <int P, int TR>
-static void set_ff_attr() {
-  cudaFuncSetAttribute(apply2d_ff_kernel<P, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)ff_smem<P, TR>());
-}
-
-template <int P>
-static bool launch_ff_P(int m, const double* bands, const StencilHost& sh, const double* w, double* y,
-                        const double* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
-                        const int* active, cudaStream_t s) {
-  constexpr int TR = 16;
-  StencilFF cs;
-  for (int x = 0; x < 3; ++x)
-    for (int k = 0; k < 13; ++k) {
-      const double v = k < 2 * P + 1 ? sh.c[x][k] : 0.0;
-      const float h = (float)v;
-      cs.c[x][k] = make_float2(h, (float)(v - (double)h));
-    }
-  cs.lo = sh.lo;
-  cs.hi = sh.hi;
-  dim3 grid((m + 63) / 64, (m + TR - 1) / TR, B);
-  apply2d_ff_kernel<P, TR><<<grid, 256, ff_smem<P, TR>(), s>>>(
-      m, sh.ffT, cs, w, y, rhs, mode, c.alpha, c.beta, c.gsc, active, dotp, g_epi<double>);
-  count_launch();
-  if (nblk) *nblk = grid.x * grid.y;
-  return true;
-}
-
-// ------------------------------------------------------------------ 2D apply in double-FP32, v2
-// The same operator and arithmetic type as apply2d_ff_kernel, rebuilt for issue rate:
-//  * the two components of a grid point travel together as packed pairs, so every double-FP32
-//    step is a packed FP32 instruction (FFMA2 / FADD2 / FMUL2) acting on (w1, w2) at once;
-//  * in the interior, where the bands equal their central rows, the symmetric M and S and the
-//    skew A are applied in folded form: c_0 x_0 + sum_t c_t (x_{-t} +- x_{+t}), the pair sums
-//    shared by M and S along x_2 (about 2/3 of the double-FP32 multiply-adds of the plain form);
-//  * shared memory rows have an odd number of 16-byte slots, so the column-wise x_2 pass (lanes
-//    = rows) and the row-wise x_1 pass (lanes = columns) are both free of bank conflicts.
-// Tile: TR = 24 (P <= 4) or 20 output rows x 32 columns per CTA of 128 threads; the x_2 pass
-// covers the TR + 2P <= 32 rows of the halo, one row per lane.
-struct FF2 {  // two double-FP32 numbers: (h.x + l.x, h.y + l.y)
-  float2 h, l;
-};
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {  // a - b, one rounding
-  return __ffma2_rn(b, f2(-1.f, -1.f), a);
-}
-__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, f2(-1.f, -1.f)); }
-// acc += c * x, c = ch + cl per lane
-__device__ __forceinline__ void ff2_fma(FF2& acc, float2 ch, float2 cl, const FF2& x) {
-  const float2 p = __fmul2_rn(ch, x.h);
-  float2 e = __ffma2_rn(ch, x.h, neg2(p));
-  e = __ffma2_rn(ch, x.l, e);
-  e = __ffma2_rn(cl, x.h, e);
-  const float2 sm = __fadd2_rn(acc.h, p);
-  const float2 bb = sub2(sm, acc.h);
-  const float2 er = __fadd2_rn(sub2(acc.h, sub2(sm, bb)), sub2(p, bb));
-  acc.l = __fadd2_rn(acc.l, __fadd2_rn(er, e));
-  acc.h = sm;
-}
-// a + b and a - b (two-sum of the high parts; low parts added)
-__device__ __forceinline__ FF2 ff2_add(const FF2& a, const FF2& b) {
-  const float2 sm = __fadd2_rn(a.h, b.h);
-  const float2 bb = sub2(sm, a.h);
-  const float2 er = __fadd2_rn(sub2(a.h, sub2(sm, bb)), sub2(b.h, bb));
-  return FF2{sm, __fadd2_rn(__fadd2_rn(a.l, b.l), er)};
-}
-__device__ __forceinline__ FF2 ff2_sub(const FF2& a, const FF2& b) {
-  const float2 sm = sub2(a.h, b.h);
-  const float2 bb = sub2(sm, a.h);
-  const float2 er = sub2(sub2(a.h, sub2(sm, bb)), __fadd2_rn(b.h, bb));
-  return FF2{sm, __fadd2_rn(sub2(a.l, b.l), er)};
-}
-__device__ __forceinline__ FF2 ff2_norm(const FF2& a) {
-  const float2 sm = __fadd2_rn(a.h, a.l);
-  return FF2{sm, sub2(a.l, sub2(sm, a.h))};
-}
-// (ch + cl) * x, normalised
-__device__ __forceinline__ FF2 ff2_mul(float2 ch, float2 cl, const FF2& x) {
-  const float2 p = __fmul2_rn(ch, x.h);
-  float2 e = __ffma2_rn(ch, x.h, neg2(p));
-  e = __ffma2_rn(ch, x.l, e);
-  e = __ffma2_rn(cl, x.h, e);
-  return ff2_norm(FF2{p, e});
-}
-__device__ __forceinline__ FF2 ld_ff2(const float4* p) {
-  const float4 v = *p;
-  return FF2{f2(v.x, v.y), f2(v.z, v.w)};
-}
-__device__ __forceinline__ void st_ff2(float4* p, const FF2& a) {
-  *p = make_float4(a.h.x, a.h.y, a.l.x, a.l.y);
-}
-
-struct StencilFF2 {
-  float c[3][2][13];  // [M, A, S][hi, lo][offset k = 0..2P], central rows
-  int lo, hi;
-};
-
-template <int P>
-struct FF2Tile {
-  static constexpr int W = 2 * P + 1;
-  static constexpr int TC = 32;
-  static constexpr int TR = P <= 4 ? 24 : 20;
-  static constexpr int HR = TR + 2 * P;           // <= 32
-  static constexpr int HC = TC + 2 * P;
-  static constexpr int HCP = HC | 1;              // input row stride in float4 slots (odd)
-  static constexpr int TCP = TC + 1;              // intermediate row stride (odd)
-  static constexpr int NC = 4;                    // columns per lane in the x_2 pass
-  static constexpr int RS = TR / 4;               // rows per lane in the x_1 pass
-  // input tile | intermediates | band rows of the tile's columns (boundary tiles); the band rows
-  // of the tile's rows reuse the input tile's space in the x_1 pass
-  static constexpr size_t off_mid = sizeof(float4) * HR * HCP;
-  static constexpr size_t off_col = off_mid + sizeof(float4) * 3 * HR * TCP;
-  static constexpr size_t smem = off_col + sizeof(float2) * 3 * W * TC;
-  static_assert(sizeof(float2) * 3 * W * TR <= off_mid, "row coefficients fit the input tile");
-};
-
-// y (or the residual, or the fused Chebyshev step) at one grid point from its double-FP32 pair
-__device__ __forceinline__ void ff2_emit(const FF2& yy, long long o1, long long o2, int mode,
-                                         const double* __restrict__ w, double* __restrict__ y,
-                                         const double* __restrict__ rhs, const Epi<double>& epi,
-                                         double ec1, double ec2, const double* dotp, double& acc) {
-  const FF2 yn = ff2_norm(yy);
-  if (mode == 2) {
-    // fused Chebyshev step: r = rhs - A w in double-FP32, the correction d = c2 D^{-1} r
-    // (+ c1 d_prev) in FP32 (a smoother step needs no more), x = x_prev + d with one FP64 add
-    const float2 q1 = ff_split_bits(rhs[o1]), q2 = ff_split_bits(rhs[o2]);
-    const FF2 rn = ff2_norm(ff2_sub(FF2{f2(q1.x, q2.x), f2(q1.y, q2.y)}, yn));
-    const float c2 = (float)ec2, c1 = (float)ec1;
-    float d1 = c2 * ff_split_bits(epi.dinv[o1]).x * rn.h.x;
-    float d2 = c2 * ff_split_bits(epi.dinv[o2]).x * rn.h.y;
-    if (epi.step > 0) {
-      d1 = fmaf(c1, ff_split_bits(epi.dprev[o1]).x, d1);
-      d2 = fmaf(c1, ff_split_bits(epi.dprev[o2]).x, d2);
-    }
-    const double e1 = f2d_bits(d1), e2 = f2d_bits(d2);
-    epi.xout[o1] = __dadd_rn(epi.xprev[o1], e1);
-    epi.xout[o2] = __dadd_rn(epi.xprev[o2], e2);
-    if (epi.dout) {
-      epi.dout[o1] = e1;
-      epi.dout[o2] = e2;
-    }
-    if (epi.rout) {
-      epi.rout[o1] = __dadd_rn(f2d_bits(rn.h.x), f2d_bits(rn.l.x));
-      epi.rout[o2] = __dadd_rn(f2d_bits(rn.h.y), f2d_bits(rn.l.y));
-    }
-    return;
-  }
-  double y1 = __dadd_rn(f2d_bits(yn.h.x), f2d_bits(yn.l.x));
-  double y2 = __dadd_rn(f2d_bits(yn.h.y), f2d_bits(yn.l.y));
-  if (mode == 1) {
-    y1 = rhs[o1] - y1;
-    y2 = rhs[o2] - y2;
-    if (dotp) acc += y1 * y1 + y2 * y2;
-  } else if (dotp) {
-    acc += w[o1] * y1 + w[o2] * y2;
-  }
-  y[o1] = y1;
-  y[o2] = y2;
-}
-
-template <int P, int MODE>
-__global__ void __launch_bounds__(128, 3) apply2d_ff2_kernel(
-    int m, const float2* __restrict__ bandF, StencilFF2 cs, const double* __restrict__ w,
-    double* __restrict__ y, const double* __restrict__ rhs, int /*mode: MODE*/,
-    const double* __restrict__ alpha, const double* __restrict__ beta,
-    const double* __restrict__ gsc, const int* __restrict__ active, double* __restrict__ dotp,
-    Epi<double> epi) {
-  using G = FF2Tile<P>;
-  constexpr int W = G::W, TC = G::TC, TR = G::TR, HR = G::HR, HC = G::HC, HCP = G::HCP;
-  constexpr int TCP = G::TCP, NC = G::NC, RS = G::RS;
-  const int b = blockIdx.z;
-  if (active && !active[b]) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float4* sIn = reinterpret_cast<float4*>(smem_raw);                   // [HR][HCP]
-  float4* sMid = reinterpret_cast<float4*>(smem_raw + G::off_mid);     // [3][HR][TCP]
-  float2* sCol = reinterpret_cast<float2*>(smem_raw + G::off_col);     // [3][W][TC]
-  float2* sRow = reinterpret_cast<float2*>(smem_raw);                  // [3][W][TR] (x_1 pass)
-  const long long N = 2LL * m * m;
-  const double* wb = w + (long long)b * N;
-  const int c0 = blockIdx.x * TC, r0 = blockIdx.y * TR;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool bcol = c0 < cs.lo || c0 + TC > cs.hi;  // tile holds non-Toeplitz columns
-  const bool brow = r0 < cs.lo || r0 + TR > cs.hi;  // ... or rows
-  {  // every load of the tile in flight before the first split (one memory latency per tile)
-    constexpr int NE = (HR * HC + 127) / 128;
-    double v1[NE], v2[NE];
-#pragma unroll
-    for (int t = 0; t < NE; ++t) {
-      const int idx = threadIdx.x + 128 * t;
-      const int rr = idx / HC, cc = idx - rr * HC;
-      const int row = r0 - P + rr, col = c0 - P + cc;
-      v1[t] = v2[t] = 0.0;
-      if (idx < HR * HC && row >= 0 && row < m && col >= 0 && col < m) {
-        const long long o = (long long)row * m + col;
-        v1[t] = wb[o];
-        v2[t] = wb[(long long)m * m + o];
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < NE; ++t) {
-      const int idx = threadIdx.x + 128 * t;
-      const int rr = idx / HC, cc = idx - rr * HC;
-      const float2 a = ff_split_bits(v1[t]), c = ff_split_bits(v2[t]);
-      if (idx < HR * HC) sIn[rr * HCP + cc] = make_float4(a.x, c.x, a.y, c.y);
-    }
-  }
-  if (bcol) {
-    constexpr int NK = (3 * W * TC + 127) / 128;
-    float2 v[NK];
-#pragma unroll
-    for (int t = 0; t < NK; ++t) {
-      const int idx = threadIdx.x + 128 * t;
-      const int xk = idx / TC, cc = idx - xk * TC;
-      v[t] = idx < 3 * W * TC && c0 + cc < m ? bandF[(size_t)xk * m + c0 + cc] : f2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int t = 0; t < NK; ++t)
-      if (threadIdx.x + 128 * t < 3 * W * TC) sCol[threadIdx.x + 128 * t] = v[t];
-  }
-  // per-solve scalars as (hi, lo) pairs, split once per CTA (FP64 work stays off the threads)
-  __shared__ float2 s_par[3];
-  if (threadIdx.x == 0) {
-    s_par[0] = ff_split(alpha[b]);
-    s_par[1] = ff_split(beta[b]);
-    s_par[2] = ff_split((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
-  }
-  __syncthreads();
-  const float2 al = s_par[0], be = s_par[1], ga = s_par[2];
-  const float2 pmh = f2(al.x, be.x), pml = f2(al.y, be.y);  // PM = (alpha, beta) * S2 w
-  const float2 psh = f2(be.x, al.x), psl = f2(be.y, al.y);  // PS = (beta, alpha) * M2 w
-  const float2 gah = f2(ga.x, ga.x), gal = f2(ga.y, ga.y);  // PA = gamma * swap(A2 w)
-  // ---- axis x_2: lane = halo row q, NC consecutive columns per step
-  if (lane < HR) {
-    const int q = lane;
-    const int row = r0 - P + q;
-    const bool rowok = row >= 0 && row < m;
-    for (int g = warp; g < TC / NC; g += 4) {
-      const int j0 = c0 + g * NC;
-      if (rowok && j0 < m && j0 >= cs.lo && j0 + NC - 1 < cs.hi) {
-        FF2 x[NC + 2 * P];
-#pragma unroll
-        for (int t = 0; t < NC + 2 * P; ++t) x[t] = ld_ff2(&sIn[q * HCP + g * NC + t]);
-#pragma unroll
-        for (int u = 0; u < NC; ++u) {
-          FF2 tM{f2(0.f, 0.f), f2(0.f, 0.f)}, tS = tM, tA = tM;
-          const FF2& xc = x[u + P];
-          ff2_fma(tM, f2(cs.c[0][0][P], cs.c[0][0][P]), f2(cs.c[0][1][P], cs.c[0][1][P]), xc);
-          ff2_fma(tS, f2(cs.c[2][0][P], cs.c[2][0][P]), f2(cs.c[2][1][P], cs.c[2][1][P]), xc);
-#pragma unroll
-          for (int t = 1; t <= P; ++t) {
-            const FF2 sp = ff2_add(x[u + P - t], x[u + P + t]);
-            const FF2 dp = ff2_sub(x[u + P + t], x[u + P - t]);
-            const int k = P + t;
-            ff2_fma(tM, f2(cs.c[0][0][k], cs.c[0][0][k]), f2(cs.c[0][1][k], cs.c[0][1][k]), sp);
-            ff2_fma(tS, f2(cs.c[2][0][k], cs.c[2][0][k]), f2(cs.c[2][1][k], cs.c[2][1][k]), sp);
-            ff2_fma(tA, f2(cs.c[1][0][k], cs.c[1][0][k]), f2(cs.c[1][1][k], cs.c[1][1][k]), dp);
-          }
-          const int cc = g * NC + u;
-          tS = ff2_norm(tS);
-          tM = ff2_norm(tM);
-          tA = ff2_norm(tA);
-          st_ff2(&sMid[(0 * HR + q) * TCP + cc], ff2_mul(pmh, pml, tS));
-          st_ff2(&sMid[(1 * HR + q) * TCP + cc], ff2_mul(psh, psl, tM));
-          st_ff2(&sMid[(2 * HR + q) * TCP + cc],
-                 ff2_mul(gah, gal, FF2{f2(tA.h.y, tA.h.x), f2(tA.l.y, tA.l.x)}));
-        }
-      } else {  // boundary columns (band rows staged in shared memory) or outside the domain
-#pragma unroll 1
-        for (int u = 0; u < NC; ++u) {
-          const int cc = g * NC + u;
-          FF2 tM{f2(0.f, 0.f), f2(0.f, 0.f)}, tS = tM, tA = tM;
-          if (rowok && c0 + cc < m) {
-#pragma unroll 1
-            for (int k = 0; k < W; ++k) {
-              const FF2 xv = ld_ff2(&sIn[q * HCP + cc + k]);
-              const float2 cM = sCol[(0 * W + k) * TC + cc], cA = sCol[(1 * W + k) * TC + cc],
-                           cS = sCol[(2 * W + k) * TC + cc];
-              ff2_fma(tM, f2(cM.x, cM.x), f2(cM.y, cM.y), xv);
-              ff2_fma(tA, f2(cA.x, cA.x), f2(cA.y, cA.y), xv);
-              ff2_fma(tS, f2(cS.x, cS.x), f2(cS.y, cS.y), xv);
-            }
-          }
-          tS = ff2_norm(tS);
-          tM = ff2_norm(tM);
-          tA = ff2_norm(tA);
-          st_ff2(&sMid[(0 * HR + q) * TCP + cc], ff2_mul(pmh, pml, tS));
-          st_ff2(&sMid[(1 * HR + q) * TCP + cc], ff2_mul(psh, psl, tM));
-          st_ff2(&sMid[(2 * HR + q) * TCP + cc],
-                 ff2_mul(gah, gal, FF2{f2(tA.h.y, tA.h.x), f2(tA.l.y, tA.l.x)}));
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (brow) {  // band rows of the tile's rows, into the input tile's space
-    constexpr int NK = (3 * W * TR + 127) / 128;
-    float2 v[NK];
-#pragma unroll
-    for (int t = 0; t < NK; ++t) {
-      const int idx = threadIdx.x + 128 * t;
-      const int xk = idx / TR, rr = idx - xk * TR;
-      v[t] = idx < 3 * W * TR && r0 + rr < m ? bandF[(size_t)xk * m + r0 + rr] : f2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int t = 0; t < NK; ++t)
-      if (threadIdx.x + 128 * t < 3 * W * TR) sRow[threadIdx.x + 128 * t] = v[t];
-    __syncthreads();
-  }
-  // ---- axis x_1: lane = column, RS rows per warp: y = M1 PM + S1 PS + A1 PA
-  double acc = 0.0, ec1 = 0.0, ec2 = 0.0;
-  if (MODE == 2) cheb_coef_cta(epi.lmax[b], epi.step, ec1, ec2);
-  const int cc = lane, j = c0 + cc;
-  const int rb = warp * RS;
-  if (j < m) {
-    if (r0 + rb >= cs.lo && r0 + rb + RS - 1 < cs.hi) {
-      FF2 yy[RS];
-#pragma unroll
-      for (int r = 0; r < RS; ++r) yy[r] = FF2{f2(0.f, 0.f), f2(0.f, 0.f)};
-#pragma unroll 1
-      for (int band = 0; band < 2; ++band) {  // M on PM, S on PS (symmetric)
-        const int x = band == 0 ? 0 : 2;
-        FF2 v[RS + 2 * P];
-#pragma unroll
-        for (int t = 0; t < RS + 2 * P; ++t) v[t] = ld_ff2(&sMid[(band * HR + rb + t) * TCP + cc]);
-        float ch[P + 1], cl[P + 1];
-#pragma unroll
-        for (int t = 0; t <= P; ++t) {
-          ch[t] = x == 0 ? cs.c[0][0][P + t] : cs.c[2][0][P + t];
-          cl[t] = x == 0 ? cs.c[0][1][P + t] : cs.c[2][1][P + t];
-        }
-#pragma unroll
-        for (int r = 0; r < RS; ++r) {
-          ff2_fma(yy[r], f2(ch[0], ch[0]), f2(cl[0], cl[0]), v[r + P]);
-#pragma unroll
-          for (int t = 1; t <= P; ++t)
-            ff2_fma(yy[r], f2(ch[t], ch[t]), f2(cl[t], cl[t]), ff2_add(v[r + P - t], v[r + P + t]));
-        }
-      }
-      {  // A on PA (skew)
-        FF2 v[RS + 2 * P];
-#pragma unroll
-        for (int t = 0; t < RS + 2 * P; ++t) v[t] = ld_ff2(&sMid[(2 * HR + rb + t) * TCP + cc]);
-#pragma unroll
-        for (int r = 0; r < RS; ++r)
-#pragma unroll
-          for (int t = 1; t <= P; ++t)
-            ff2_fma(yy[r], f2(cs.c[1][0][P + t], cs.c[1][0][P + t]),
-                    f2(cs.c[1][1][P + t], cs.c[1][1][P + t]), ff2_sub(v[r + P + t], v[r + P - t]));
-      }
-#pragma unroll
-      for (int r = 0; r < RS; ++r) {
-        const long long o1 = (long long)b * N + (long long)(r0 + rb + r) * m + j;
-        ff2_emit(yy[r], o1, o1 + (long long)m * m, MODE, w, y, rhs, epi, ec1, ec2, dotp, acc);
-      }
-    } else {  // boundary rows (band rows staged in shared memory)
-#pragma unroll 1
-      for (int r = 0; r < RS; ++r) {
-        const int i = r0 + rb + r;
-        if (i >= m) break;
-        FF2 yy{f2(0.f, 0.f), f2(0.f, 0.f)};
-#pragma unroll 1
-        for (int band = 0; band < 3; ++band) {
-          const int x = band == 0 ? 0 : band == 1 ? 2 : 1;
-#pragma unroll 1
-          for (int k = 0; k < W; ++k) {
-            const float2 cX = sRow[(x * W + k) * TR + rb + r];
-            ff2_fma(yy, f2(cX.x, cX.x), f2(cX.y, cX.y), ld_ff2(&sMid[(band * HR + rb + r + k) * TCP + cc]));
-          }
-        }
-        const long long o1 = (long long)b * N + (long long)i * m + j;
-        ff2_emit(yy, o1, o1 + (long long)m * m, MODE, w, y, rhs, epi, ec1, ec2, dotp, acc);
-      }
-    }
-  }
-  if (dotp) {
-    const double sum = block_sum(acc);
-    if (threadIdx.x == 0)
-      dotp[(size_t)b * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = sum;
-  }
-}
-
-template <int P>
-static void set_ff2_attr() {
-  cudaFuncSetAttribute(apply2d_ff2_kernel<P, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)FF2Tile<P>::smem);
-  cudaFuncSetAttribute(apply2d_ff2_kernel<P, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)FF2Tile<P>::smem);
-  cudaFuncSetAttribute(apply2d_ff2_kernel<P, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)FF2Tile<P>::smem);
-}
-
-// Central rows split into (hi, lo); false unless M and S are palindromes and A is skew with a
-// zero centre (the folded interior form needs that exactly).
-static bool stencil_ff2(const StencilHost& sh, StencilFF2& cs) {
-  const int P = sh.P;
-  if (!stencil_folds(sh)) return false;
-  for (int x = 0; x < 3; ++x)
-    for (int k = 0; k < 13; ++k) {
-      const double v = k < 2 * P + 1 ? sh.c[x][k] : 0.0;
-      const float h = (float)v;
-      cs.c[x][0][k] = h;
-      cs.c[x][1][k] = (float)(v - (double)h);
-    }
-  cs.lo = sh.lo;
-  cs.hi = sh.hi;
-  return true;
-}
-
-template <int P>
-static bool launch_ff2_P(int m, const StencilHost& sh, const double* w, double* y,
-                         const double* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
-                         const int* active, cudaStream_t s) {
-  using G = FF2Tile<P>;
-  StencilFF2 cs;
-  if (!stencil_ff2(sh, cs)) return false;
-  dim3 grid((m + G::TC - 1) / G::TC, (m + G::TR - 1) / G::TR, B);
-  if (dotp && (long long)grid.x * grid.y > kMaxPartials) return false;
-  // one instantiation per epilogue mode keeps each kernel's code within the instruction cache
-  if (mode == 0)
-    apply2d_ff2_kernel<P, 0><<<grid, 128, G::smem, s>>>(m, sh.ffT, cs, w, y, rhs, mode, c.alpha,
-                                                        c.beta, c.gsc, active, dotp, g_epi<double>);
-  else if (mode == 1)
-    apply2d_ff2_kernel<P, 1><<<grid, 128, G::smem, s>>>(m, sh.ffT, cs, w, y, rhs, mode, c.alpha,
-                                                        c.beta, c.gsc, active, dotp, g_epi<double>);
-  else
-    apply2d_ff2_kernel<P, 2><<<grid, 128, G::smem, s>>>(m, sh.ffT, cs, w, y, rhs, mode, c.alpha,
-                                                        c.beta, c.gsc, active, dotp, g_epi<double>);
-  count_launch();
-  if (nblk) *nblk = grid.x * grid.y;
-  return true;
-}
-
 static thread_local int g_ff_inner = 0;  // the calling thread's FP64 applies run in double-FP32
 void set_fp64_emulated(int on) { g_ff_inner = on; }
 int fp64_emulated() { return g_ff_inner || g_ff_forced; }
-
-static bool try_apply2d_ff(int m, int P, const double* bands, const double* w, double* y,
-                           const double* rhs, int mode, int B, Coef c, double* dotp, int* nblk,
-                           const int* active, cudaStream_t s) {
-  if (mode == 2 && !g_epi<double>.dinv) return false;
-  StencilHost sh;
-  if (!find_level(bands, sh) || sh.P != P || !sh.ffT) return false;
-  if (g_ff_kernel == 2) {
-    bool ok = false;
-    switch (P) {
-      case 1: ok = launch_ff2_P<1>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
-      case 2: ok = launch_ff2_P<2>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
-      case 3: ok = launch_ff2_P<3>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
-      case 4: ok = launch_ff2_P<4>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
-      case 5: ok = launch_ff2_P<5>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
-      case 6: ok = launch_ff2_P<6>(m, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s); break;
-      default: break;
-    }
-    if (ok) return true;
-  }
-  if (dotp && (long long)((m + 63) / 64) * ((m + 15) / 16) > kMaxPartials) return false;
-  switch (P) {
-    case 1: return launch_ff_P<1>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
-    case 2: return launch_ff_P<2>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
-    case 3: return launch_ff_P<3>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
-    case 4: return launch_ff_P<4>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
-    case 5: return launch_ff_P<5>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
-    case 6: return launch_ff_P<6>(m, bands, sh, w, y, rhs, mode, B, c, dotp, nblk, active, s);
-    default: return false;
-  }
-}
 
 int prepare_kernels() {
   set_stream3d_attr<float, 1>(); set_stream3d_attr<float, 2>(); set_stream3d_attr<float, 3>();
@@ -2417,333 +1717,14 @@ int prepare_kernels() {
   set_v2_attrs<float, 4>(); set_v2_attrs<float, 5>(); set_v2_attrs<float, 6>();
   set_v2_attrs<double, 1>(); set_v2_attrs<double, 2>(); set_v2_attrs<double, 3>();
   set_v2_attrs<double, 4>(); set_v2_attrs<double, 5>(); set_v2_attrs<double, 6>();
-  set_ff_attr<1, 16>(); set_ff_attr<2, 16>(); set_ff_attr<3, 16>();
-  set_ff_attr<4, 16>(); set_ff_attr<5, 16>(); set_ff_attr<6, 16>();
   set_v5_attr<1>(); set_v5_attr<2>(); set_v5_attr<3>();
   set_v5_attr<4>(); set_v5_attr<5>(); set_v5_attr<6>();
-  set_ff2_attr<1>(); set_ff2_attr<2>(); set_ff2_attr<3>();
-  set_ff2_attr<4>(); set_ff2_attr<5>(); set_ff2_attr<6>();
+  prepare_ff_kernels();
   cudaError_t e1 = cudaFuncSetAttribute(apply2d_kernel<double>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmemCap);
   cudaError_t e2 = cudaFuncSetAttribute(apply2d_kernel<float>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kApplySmemCap);
   return (e1 == cudaSuccess && e2 == cudaSuccess) ? 0 : 1;
-}
-
-// ------------------------------------------------------------------ 3D apply: three tuned passes
-// The three banded passes of the 3D operator (x_3: nine arrays T_{X,c} = X_3 w_c; x_2: nine
-// arrays P grouped by the x_1 operator they feed; x_1: y_c = M_1 P_cM + S_1 P_cS + A_1 P_cA),
-// each a kernel with the minimal 33 (2p+1) multiply-adds per grid point: along x_2 and x_1 a
-// thread produces R consecutive rows from one register window of R + 2P inputs per array
-// (coalesced across the warp along x_3), along x_3 one point from a window read through L1.
-// Interior rows take the central stencil from the kernel parameters, boundary rows their band
-// row.  Three arithmetic policies: FP32, FP64, and double-FP32 (FP64 input and output, the
-// intermediates stored as (hi, lo) FP32 pairs, every multiply-add a double-FP32 one on the FP32
-// pipe).
-struct P3F32 {
-  using In = float;
-  using Mid = float;
-  using V = float;
-  using C = float;
-  static __device__ __forceinline__ V zero() { return 0.f; }
-  static __device__ __forceinline__ V in(const In* p) { return *p; }
-  static __device__ __forceinline__ V mid(const Mid* p) { return *p; }
-  static __device__ __forceinline__ void put_mid(Mid* p, V v) { *p = v; }
-  static __device__ __forceinline__ In out(V v) { return v; }
-  static __device__ __forceinline__ void fma(V& acc, C c, V x) { acc = fmaf(c, x, acc); }
-  static __device__ __forceinline__ V mul(C c, V x) { return c * x; }
-  static __device__ __forceinline__ C band(const float* bands, size_t i) { return bands[i]; }
-  static __host__ __device__ __forceinline__ C cst(double v) { return (float)v; }
-};
-struct P3F64 {
-  using In = double;
-  using Mid = double;
-  using V = double;
-  using C = double;
-  static __device__ __forceinline__ V zero() { return 0.0; }
-  static __device__ __forceinline__ V in(const In* p) { return *p; }
-  static __device__ __forceinline__ V mid(const Mid* p) { return *p; }
-  static __device__ __forceinline__ void put_mid(Mid* p, V v) { *p = v; }
-  static __device__ __forceinline__ In out(V v) { return v; }
-  static __device__ __forceinline__ void fma(V& acc, C c, V x) { acc = ::fma(c, x, acc); }
-  static __device__ __forceinline__ V mul(C c, V x) { return c * x; }
-  static __device__ __forceinline__ C band(const double* bands, size_t i) { return bands[i]; }
-  static __host__ __device__ __forceinline__ C cst(double v) { return v; }
-};
-struct P3FF {
-  using In = double;
-  using Mid = float2;
-  using V = float2;  // (hi, lo)
-  using C = float2;
-  static __device__ __forceinline__ V zero() { return make_float2(0.f, 0.f); }
-  static __device__ __forceinline__ V in(const In* p) { return ff_split_bits(*p); }
-  static __device__ __forceinline__ V mid(const Mid* p) { return *p; }
-  static __device__ __forceinline__ void put_mid(Mid* p, V v) { *p = ff_norm(v); }
-  static __device__ __forceinline__ In out(V v) {
-    const float2 n = ff_norm(v);
-    return __dadd_rn(f2d_bits(n.x), f2d_bits(n.y));
-  }
-  static __device__ __forceinline__ void fma(V& acc, C c, V x) { ff_fma(acc, c, x); }
-  static __device__ __forceinline__ V mul(C c, V x) { return ff_mul(c, x); }
-  static __device__ __forceinline__ C band(const double* bands, size_t i) {
-    return ff_split_bits(bands[i]);
-  }
-  static __host__ __device__ __forceinline__ C cst(double v) {
-    const float h = (float)v;
-    return make_float2(h, (float)(v - (double)h));
-  }
-};
-__device__ __forceinline__ float add3(float a, float b) { return a + b; }
-__device__ __forceinline__ double add3(double a, double b) { return a + b; }
-__device__ __forceinline__ float2 add3(float2 a, float2 b) {  // double-FP32 a + b
-  const float sm = __fadd_rn(a.x, b.x);
-  const float bb = __fsub_rn(sm, a.x);
-  const float er = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sm, bb)), __fsub_rn(b.x, bb));
-  return make_float2(sm, __fadd_rn(__fadd_rn(a.y, b.y), er));
-}
-
-template <typename Pol>
-struct Stencil3 {
-  typename Pol::C c[3][13];  // M, A, S central rows
-  int lo, hi;
-};
-template <typename Pol>
-struct Pass3Args {
-  const typename Pol::In* w;   // [B][3][m^3] (pass 0)
-  const float2* wsplit;        // double-FP32 policy: w split into (hi, lo) pairs, same layout
-  typename Pol::Mid* t;        // 9 arrays [9][B][m^3] (pass 0 out, pass 1 in)
-  typename Pol::Mid* q;        // 9 arrays (pass 1 out, pass 2 in)
-  typename Pol::In* y;         // [B][3][m^3] (pass 2)
-};
-
-// band X applied along an axis to a window of R + 2P values:
-// out[r] = (scaled ? scale : 1) * sum_k X(i0 + r, i0 + r - P + k) win[r + k]
-template <typename Pol, int P, int R>
-__device__ __forceinline__ void band_apply(const Stencil3<Pol>& cs, const typename Pol::In* bands,
-                                           int m, int X, int i0, const typename Pol::V* win,
-                                           typename Pol::C scale, bool scaled, typename Pol::V* out) {
-  constexpr int W = 2 * P + 1;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int i = i0 + r;
-    typename Pol::V acc = Pol::zero();
-    if (i >= cs.lo && i < cs.hi) {
-#pragma unroll
-      for (int k = 0; k < W; ++k) Pol::fma(acc, cs.c[X][k], win[r + k]);
-    } else if (i < m) {
-#pragma unroll
-      for (int k = 0; k < W; ++k) Pol::fma(acc, Pol::band(bands, ((size_t)X * m + i) * W + k), win[r + k]);
-    }
-    out[r] = scaled ? Pol::mul(scale, acc) : acc;
-  }
-}
-
-template <typename Pol, int P, int PASS, int R>
-__global__ void __launch_bounds__(128) pass3d_kernel(int m, const typename Pol::In* __restrict__ bands,
-                                                     Stencil3<Pol> cs, Pass3Args<Pol> a,
-                                                     const double* __restrict__ alpha,
-                                                     const double* __restrict__ beta,
-                                                     const double* __restrict__ gsc,
-                                                     const int* __restrict__ active) {
-  using V = typename Pol::V;
-  using C = typename Pol::C;
-  const int b = blockIdx.y;
-  if (active && !active[b]) return;
-  __shared__ C s_par[3];
-  if (threadIdx.x == 0) {
-    s_par[0] = Pol::cst(alpha[b]);
-    s_par[1] = Pol::cst(beta[b]);
-    s_par[2] = Pol::cst((alpha[b] - beta[b]) * (gsc ? gsc[b] : 1.0));
-  }
-  __syncthreads();
-  const C al = s_par[0], be = s_par[1], ga = s_par[2];
-  const int n3 = m * m * m, nblk = (m + R - 1) / R;
-  const int stride = PASS == 0 ? 1 : PASS == 1 ? m : m * m;
-  const int items = PASS == 0 ? n3 : nblk * m * m;
-  const long long B = gridDim.y;
-  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
-    // (i0, i1, i2) of the first row this thread produces; the pass axis is blocked by R
-    int i0, i1, i2;
-    if (PASS == 0) {
-      i2 = it % m;
-      i1 = (it / m) % m;
-      i0 = it / (m * m);
-    } else if (PASS == 1) {
-      i2 = it % m;
-      i1 = ((it / m) % nblk) * R;
-      i0 = it / (m * nblk);
-    } else {
-      i2 = it % m;
-      i1 = (it / m) % m;
-      i0 = (it / (m * m)) * R;
-    }
-    const int ia = PASS == 0 ? i2 : PASS == 1 ? i1 : i0;  // position along the pass axis
-    const int base = (i0 * m + i1) * m + i2;              // point of the first row
-    auto window = [&](auto loader, V* win) {
-#pragma unroll
-      for (int k = 0; k < R + 2 * P; ++k) {
-        const int j = ia - P + k;
-        win[k] = (j >= 0 && j < m) ? loader(base + (k - P) * stride) : Pol::zero();
-      }
-    };
-    if constexpr (PASS == 0) {
-      V win[R + 2 * P], o[R];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if constexpr (std::is_same<V, float2>::value) {  // split once by the split kernel
-          const float2* wc = a.wsplit + ((long long)b * 3 + c) * n3;
-          window([&](int idx) { return wc[idx]; }, win);
-        } else {
-          const typename Pol::In* wc = a.w + ((long long)b * 3 + c) * n3;
-          window([&](int idx) { return Pol::in(wc + idx); }, win);
-        }
-#pragma unroll
-        for (int X = 0; X < 3; ++X) {
-          band_apply<Pol, P, R>(cs, bands, m, X, ia, win, al, false, o);
-          Pol::put_mid(a.t + ((long long)(X * 3 + c) * B + b) * n3 + base, o[0]);
-        }
-      }
-    } else if constexpr (PASS == 1 && std::is_same<V, float2>::value) {
-      // double-FP32: one output at a time (its terms' windows reloaded), few live registers
-      V win[R + 2 * P], tmp[R], acc[R];
-      auto term = [&](int X, int comp, int X2, C sc, bool first) {
-        const typename Pol::Mid* src = a.t + ((long long)(X * 3 + comp) * B + b) * n3;
-        window([&](int idx) { return Pol::mid(src + idx); }, win);
-        band_apply<Pol, P, R>(cs, bands, m, X2, ia, win, sc, true, tmp);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = first ? tmp[r] : add3(acc[r], tmp[r]);
-      };
-      auto store = [&](int o) {
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (ia + r < m) Pol::put_mid(a.q + ((long long)o * B + b) * n3 + base + r * stride, acc[r]);
-      };
-      term(2, 0, 0, al, true); term(0, 0, 2, al, false); store(0);   // P1M
-      term(0, 0, 0, be, true); store(1);                             // P1S
-      term(0, 1, 1, ga, true); term(1, 2, 0, ga, false); store(2);   // P1A
-      term(2, 1, 0, al, true); term(0, 1, 2, be, false); term(1, 2, 1, ga, false); store(3);  // P2M
-      term(0, 1, 0, al, true); store(4);                             // P2S
-      term(0, 0, 1, ga, true); store(5);                             // P2A
-      term(0, 2, 2, al, true); term(2, 2, 0, be, false); term(1, 1, 1, ga, false); store(6);  // P3M
-      term(0, 2, 0, al, true); store(7);                             // P3S
-      term(1, 0, 0, ga, true); store(8);                             // P3A
-    } else if constexpr (PASS == 1) {
-      // P_cX arrays (index c*3 + {0: feeds M1, 1: feeds S1, 2: feeds A1}) from the T arrays
-      // (index X*3 + comp, X: 0 M, 1 A, 2 S):
-      // P1M = alpha (M2 T_S1 + S2 T_M1); P1S = beta M2 T_M1; P1A = gamma (A2 T_M2 + M2 T_A3)
-      // P2M = alpha M2 T_S2 + beta S2 T_M2 + gamma A2 T_A3; P2S = alpha M2 T_M2; P2A = gamma A2 T_M1
-      // P3M = alpha S2 T_M3 + beta M2 T_S3 + gamma A2 T_A2; P3S = alpha M2 T_M3; P3A = gamma M2 T_A1
-      V acc[9][R];
-#pragma unroll
-      for (int o = 0; o < 9; ++o)
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[o][r] = Pol::zero();
-      V win[R + 2 * P], tmp[R];
-      auto from = [&](int X, int comp) {
-        const typename Pol::Mid* src = a.t + ((long long)(X * 3 + comp) * B + b) * n3;
-        window([&](int idx) { return Pol::mid(src + idx); }, win);
-      };
-      auto addto = [&](int o, int X2, C sc) {  // acc[o] += sc * X2_2 win
-        band_apply<Pol, P, R>(cs, bands, m, X2, ia, win, sc, true, tmp);
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[o][r] = add3(acc[o][r], tmp[r]);
-      };
-      from(2, 0); addto(0, 0, al);                                   // T_S1
-      from(0, 0); addto(0, 2, al); addto(1, 0, be); addto(5, 1, ga); // T_M1
-      from(0, 1); addto(2, 1, ga); addto(3, 2, be); addto(4, 0, al); // T_M2
-      from(1, 2); addto(2, 0, ga); addto(3, 1, ga);                  // T_A3
-      from(2, 1); addto(3, 0, al);                                   // T_S2
-      from(0, 2); addto(6, 2, al); addto(7, 0, al);                  // T_M3
-      from(2, 2); addto(6, 0, be);                                   // T_S3
-      from(1, 1); addto(6, 1, ga);                                   // T_A2
-      from(1, 0); addto(8, 0, ga);                                   // T_A1
-#pragma unroll
-      for (int o = 0; o < 9; ++o)
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (ia + r < m) Pol::put_mid(a.q + ((long long)o * B + b) * n3 + base + r * stride, acc[o][r]);
-    } else {
-      V win[R + 2 * P], tmp[R];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        V yc[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) yc[r] = Pol::zero();
-#pragma unroll
-        for (int g = 0; g < 3; ++g) {  // P_cM with M1, P_cS with S1, P_cA with A1
-          const typename Pol::Mid* src = a.q + ((long long)(c * 3 + g) * B + b) * n3;
-          window([&](int idx) { return Pol::mid(src + idx); }, win);
-          band_apply<Pol, P, R>(cs, bands, m, g == 0 ? 0 : g == 1 ? 2 : 1, ia, win, al, false, tmp);
-#pragma unroll
-          for (int r = 0; r < R; ++r) yc[r] = add3(yc[r], tmp[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if (ia + r < m) a.y[((long long)b * 3 + c) * n3 + base + r * stride] = Pol::out(yc[r]);
-      }
-    }
-  }
-}
-
-// (hi, lo) FP32 pairs of an FP64 array, by integer operations
-__global__ void __launch_bounds__(256) split_ff_kernel(long long n, const double* __restrict__ src,
-                                                        float2* __restrict__ dst,
-                                                        const int* __restrict__ active, long long per) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    if (active && !active[i / per]) continue;
-    dst[i] = ff_split_bits(src[i]);
-  }
-}
-
-template <typename Pol, int P>
-static void launch_pass3d_P(int m, const typename Pol::In* bands, const StencilHost& sh,
-                            const typename Pol::In* w, typename Pol::In* y, int B, Coef c,
-                            const int* active, typename Pol::Mid* scratch, cudaStream_t s) {
-  constexpr int R = 4;
-  Stencil3<Pol> cs;
-  for (int x = 0; x < 3; ++x)
-    for (int k = 0; k < 13; ++k) cs.c[x][k] = Pol::cst(k < 2 * P + 1 ? sh.c[x][k] : 0.0);
-  cs.lo = sh.lo;
-  cs.hi = sh.hi;
-  const long long n3 = (long long)m * m * m;
-  // the q arrays' space holds the split input during the first pass (q is written by the second)
-  Pass3Args<Pol> a{w, reinterpret_cast<const float2*>(scratch + 9 * n3 * B), scratch,
-                   scratch + 9 * n3 * B, y};
-  if constexpr (std::is_same<typename Pol::V, float2>::value) {
-    split_ff_kernel<<<(unsigned)std::min<long long>((3 * n3 * B + 255) / 256, 16384), 256, 0, s>>>(
-        3 * n3 * B, (const double*)w, reinterpret_cast<float2*>(scratch + 9 * n3 * B), active, 3 * n3);
-    count_launch();
-  }
-  auto grid = [&](long long items) {
-    return dim3((unsigned)std::min<long long>((items + 127) / 128, 16384), B);
-  };
-  const long long nblk = (m + R - 1) / R;
-  pass3d_kernel<Pol, P, 0, 1><<<grid(n3), 128, 0, s>>>(m, bands, cs, a, c.alpha, c.beta, c.gsc, active);
-  pass3d_kernel<Pol, P, 1, R><<<grid(nblk * m * m), 128, 0, s>>>(m, bands, cs, a, c.alpha, c.beta,
-                                                                 c.gsc, active);
-  pass3d_kernel<Pol, P, 2, R><<<grid(nblk * m * m), 128, 0, s>>>(m, bands, cs, a, c.alpha, c.beta,
-                                                                 c.gsc, active);
-  count_launch(3);
-}
-
-// y = A w (3D) by the three tuned passes; the FP64 policy P3FF computes in double-FP32.  False
-// when the level is not registered or P is outside 1..6.
-template <typename Pol>
-static bool launch_pass3d(int m, int P, const typename Pol::In* bands, const typename Pol::In* w,
-                          typename Pol::In* y, int B, Coef c, const int* active,
-                          typename Pol::Mid* scratch, cudaStream_t s) {
-  StencilHost sh;
-  if (!find_level(bands, sh) || sh.P != P) return false;
-  switch (P) {
-    case 1: launch_pass3d_P<Pol, 1>(m, bands, sh, w, y, B, c, active, scratch, s); return true;
-    case 2: launch_pass3d_P<Pol, 2>(m, bands, sh, w, y, B, c, active, scratch, s); return true;
-    case 3: launch_pass3d_P<Pol, 3>(m, bands, sh, w, y, B, c, active, scratch, s); return true;
-    case 4: launch_pass3d_P<Pol, 4>(m, bands, sh, w, y, B, c, active, scratch, s); return true;
-    case 5: launch_pass3d_P<Pol, 5>(m, bands, sh, w, y, B, c, active, scratch, s); return true;
-    case 6: launch_pass3d_P<Pol, 6>(m, bands, sh, w, y, B, c, active, scratch, s); return true;
-    default: return false;
-  }
 }
 
 template <typename T>
@@ -2776,7 +1757,8 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
   if (d == 2) {
     if constexpr (sizeof(T) == 8) {
       if (fp64_emulated() &&
-          try_apply2d_ff(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s))
+          try_apply2d_ff(m, P, bands, w, y, rhs, mode, B, c, dotp, nblk, active, s, g_epi<double>,
+                         g_ff_kernel))
         return 0;
     }
     if (sizeof(T) == 8 && g_use_v2 == 2 && g_fp64_v3 &&
@@ -2834,12 +1816,12 @@ int launch_apply(int d, int m, int P, const T* bands, const T* w, T* y, const T*
   if (g_use_pass3d) {
     if constexpr (sizeof(T) == 8) {
       if (emu3)
-        done = launch_pass3d<P3FF>(m, P, bands, w, ytmp, B, c, active,
-                                   reinterpret_cast<float2*>(scratch), s);
+        done = launch_pass3d_ff(m, P, bands, w, ytmp, B, c, active,
+                                reinterpret_cast<float2*>(scratch), s);
       else if (g_use_pass3d == 2)
-        done = launch_pass3d<P3F64>(m, P, bands, w, ytmp, B, c, active, scratch, s);
+        done = launch_pass3d_f64(m, P, bands, w, ytmp, B, c, active, scratch, s);
     } else {
-      done = launch_pass3d<P3F32>(m, P, bands, w, ytmp, B, c, active, scratch, s);
+      done = launch_pass3d_f32(m, P, bands, w, ytmp, B, c, active, scratch, s);
     }
   }
   if (!done) apply3d_multipass<T>(m, P, bands, w, ytmp, B, c, active, scratch, s);

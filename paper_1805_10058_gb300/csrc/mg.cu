@@ -379,45 +379,157 @@ __global__ void __launch_bounds__(256) coarse_solve_kernel(int nc, const T* __re
   if (lane == 0) x[(size_t)b * nc + i] = s;
 }
 
-// In-place inverse of one SPD matrix per CTA by Gauss-Jordan elimination without pivoting (the
-// pivots of an SPD matrix are positive), FP64; the FP32 copy is written at the end.  A pivot
-// that is not positive sets *bad and the CTA stops.
-__global__ void __launch_bounds__(512) spd_invert_kernel(int n, double* __restrict__ mats,
-                                                         float* __restrict__ mats32,
-                                                         int* __restrict__ bad) {
-  extern __shared__ double colk[];  // column k before the step
-  __shared__ double piv;
-  __shared__ int stop;
-  double* a = mats + (size_t)blockIdx.x * n * n;
-  if (threadIdx.x == 0) stop = 0;
-  for (int k = 0; k < n; ++k) {
+// In-place inverses of SPD matrices by blocked Gauss-Jordan elimination without pivoting (the
+// pivots of an SPD matrix, and of its Schur complements, are positive), FP64.  With the index
+// set split into the current panel P (kGJW columns) and the rest R, one block step maps
+//   A_PP -> A_PP^{-1},  A_PR -> A_PP^{-1} A_PR,  A_RP -> -A_RP A_PP^{-1},
+//   A_RR -> A_RR - A_RP A_PP^{-1} A_PR,
+// and the steps over all panels in order leave A^{-1}.  The rank-kGJW update of A_RR, all but a
+// vanishing part of the n^3 multiply-adds, is spread over 64 x 64 tiles of every matrix, so the
+// inverse runs on the whole GPU (on GB300 an SM issues about two FP64 FMAs per clock: one CTA
+// per matrix would take tens of milliseconds at n ~ 600).
+static constexpr int kGJW = 32;  // panel width
+static constexpr int kGJT = 64;  // tile of the update (rows and columns)
+static __host__ __device__ size_t gj_ws_per_matrix(int n) { return (size_t)kGJW * kGJW + 2 * (size_t)kGJW * n; }
+
+// Block step, part 1; CTA (slice, matrix): D^{-1} of the panel's diagonal block by Gauss-Jordan
+// in shared memory, U = D^{-1} A[P, slice] and the old column panel L = A[slice, P] into the
+// side buffer [D^{-1}: W x W | U: W x n | L: n x W] of the matrix.  A pivot that is not
+// positive sets *bad (the host then fails the call).
+__global__ void __launch_bounds__(256) gj_panel_kernel(int n, int k0, int w,
+                                                       const double* __restrict__ mats,
+                                                       double* __restrict__ ws,
+                                                       int* __restrict__ bad) {
+  __shared__ double sD[kGJW][kGJW + 1];
+  __shared__ double sA[kGJW][kGJT + 1];
+  __shared__ double sCol[kGJW];
+  __shared__ double sPiv;
+  const int b = blockIdx.y, c0 = blockIdx.x * kGJT;
+  const double* a = mats + (size_t)b * n * n;
+  double* inv = ws + (size_t)b * gj_ws_per_matrix(n);
+  double* U = inv + kGJW * kGJW;
+  double* L = U + (size_t)kGJW * n;
+  for (int e = threadIdx.x; e < kGJW * kGJW; e += blockDim.x) {
+    const int i = e / kGJW, j = e % kGJW;
+    sD[i][j] = (i < w && j < w) ? a[(size_t)(k0 + i) * n + k0 + j] : 0.0;
+  }
+  for (int e = threadIdx.x; e < kGJW * kGJT; e += blockDim.x) {
+    const int t = e / kGJT, jj = e % kGJT;
+    sA[t][jj] = (t < w && c0 + jj < n) ? a[(size_t)(k0 + t) * n + c0 + jj] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < w; ++k) {
     if (threadIdx.x == 0) {
-      const double akk = a[(size_t)k * n + k];
-      if (!(akk > 0.0)) {
-        stop = 1;
+      double p = sD[k][k];
+      if (!(p > 0.0)) {
         atomicExch(bad, 1);
+        p = 1.0;
       }
-      piv = 1.0 / akk;
+      sPiv = 1.0 / p;
     }
+    if (threadIdx.x < kGJW) sCol[threadIdx.x] = sD[threadIdx.x][k];
     __syncthreads();
-    if (stop) return;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) colk[i] = a[(size_t)i * n + k];
+    const double piv = sPiv;
+    if (threadIdx.x < w) sD[k][threadIdx.x] = threadIdx.x == k ? piv : sD[k][threadIdx.x] * piv;
     __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x)
-      a[(size_t)k * n + j] = j == k ? piv : a[(size_t)k * n + j] * piv;
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e / n, j = e - i * n;
-      if (i == k) continue;
-      if (j == k)
-        a[e] = -colk[i] * piv;
-      else
-        a[e] -= colk[i] * a[(size_t)k * n + j];
+    for (int e = threadIdx.x; e < kGJW * kGJW; e += blockDim.x) {
+      const int i = e / kGJW, j = e % kGJW;
+      if (i == k || i >= w || j >= w) continue;
+      sD[i][j] = j == k ? -sCol[i] * piv : sD[i][j] - sCol[i] * sD[k][j];
     }
     __syncthreads();
   }
-  float* a32 = mats32 + (size_t)blockIdx.x * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) a32[e] = (float)a[e];
+  if (blockIdx.x == 0)
+    for (int e = threadIdx.x; e < kGJW * kGJW; e += blockDim.x) inv[e] = sD[e / kGJW][e % kGJW];
+  for (int e = threadIdx.x; e < kGJW * kGJT; e += blockDim.x) {
+    const int t = e / kGJT, jj = e % kGJT;
+    if (t >= w || c0 + jj >= n) continue;
+    double acc = 0.0;
+    for (int q = 0; q < w; ++q) acc = fma(sD[t][q], sA[q][jj], acc);
+    U[(size_t)t * n + c0 + jj] = acc;
+  }
+  for (int e = threadIdx.x; e < kGJT * kGJW; e += blockDim.x) {
+    const int ii = e / kGJW, t = e % kGJW;
+    if (c0 + ii < n && t < w) L[(size_t)(c0 + ii) * kGJW + t] = a[(size_t)(c0 + ii) * n + k0 + t];
+  }
+}
+
+// Block step, part 2; CTA (column tile, row tile, matrix): the new values of a 64 x 64 tile,
+// a 4 x 4 block of outputs per thread.
+__global__ void __launch_bounds__(256) gj_update_kernel(int n, int k0, int w, double* __restrict__ mats,
+                                                        const double* __restrict__ ws) {
+  __shared__ double sL[kGJT][kGJW + 1];
+  __shared__ double sX[kGJW][kGJT + 1];
+  const int b = blockIdx.z, I = blockIdx.y * kGJT, J = blockIdx.x * kGJT;
+  double* a = mats + (size_t)b * n * n;
+  const double* inv = ws + (size_t)b * gj_ws_per_matrix(n);
+  const double* U = inv + kGJW * kGJW;
+  const double* L = U + (size_t)kGJW * n;
+  for (int e = threadIdx.x; e < kGJT * kGJW; e += blockDim.x) {
+    const int ii = e / kGJW, t = e % kGJW;
+    sL[ii][t] = (I + ii < n && t < w) ? L[(size_t)(I + ii) * kGJW + t] : 0.0;
+  }
+  for (int e = threadIdx.x; e < kGJW * kGJT; e += blockDim.x) {
+    const int t = e / kGJT, jj = e % kGJT, j = J + jj;
+    double v = 0.0;
+    if (t < w && j < n) v = (j >= k0 && j < k0 + w) ? inv[t * kGJW + (j - k0)] : U[(size_t)t * n + j];
+    sX[t][jj] = v;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int t = 0; t < w; ++t) {
+    double l[4], x[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) l[r] = sL[ty + 16 * r][t];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) x[c] = sX[t][tx + 16 * c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = fma(l[r], x[c], acc[r][c]);
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = I + ty + 16 * r;
+    if (i >= n) continue;
+    const bool ip = i >= k0 && i < k0 + w;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = J + tx + 16 * c;
+      if (j >= n) continue;
+      const bool jp = j >= k0 && j < k0 + w;
+      double& y = a[(size_t)i * n + j];
+      if (ip)
+        y = sX[i - k0][tx + 16 * c];  // D^{-1} or U
+      else
+        y = jp ? -acc[r][c] : y - acc[r][c];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) to_f32_kernel(long long n, const double* __restrict__ src,
+                                                     float* __restrict__ dst) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// nmat SPD matrices of order n (contiguous, row-major) inverted in place, the FP32 copies
+// written to mats32; *bad (device) is set for a matrix that is not SPD.  ws: nmat *
+// gj_ws_per_matrix(n) doubles.
+static void gpu_spd_invert(int n, int nmat, double* mats, float* mats32, int* bad, double* ws,
+                           cudaStream_t s) {
+  const unsigned tiles = (unsigned)((n + kGJT - 1) / kGJT);
+  for (int k0 = 0; k0 < n; k0 += kGJW) {
+    const int w = std::min(kGJW, n - k0);
+    gj_panel_kernel<<<dim3(tiles, nmat), 256, 0, s>>>(n, k0, w, mats, ws, bad);
+    gj_update_kernel<<<dim3(tiles, tiles, nmat), 256, 0, s>>>(n, k0, w, mats, ws);
+    count_launch(2);
+  }
+  const long long tot = (long long)nmat * n * n;
+  to_f32_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 8192), 256, 0, s>>>(tot, mats, mats32);
+  count_launch();
 }
 
 // ------------------------------------------------------------------ host side
@@ -512,6 +624,10 @@ cd_status mg_build(MgData& mg, int d, int P, const std::vector<int>& ml,
   mg.cinv32 = (float*)alloc(sizeof(float) * (size_t)B * mg.nc * mg.nc);
   mg.part = (double*)alloc(sizeof(double) * (size_t)B * kMaxPartials);
   mg.tmpB = (double*)alloc(sizeof(double) * B);
+  if (mg.nc >= 128) {  // side buffer of the GPU inversion of the coarsest matrices
+    mg.gjws = (double*)alloc(sizeof(double) * B * gj_ws_per_matrix(mg.nc));
+    if (!mg.gjws) return CD_ENOMEM;
+  }
   // 3D scratch for levels >= 1 (the finest level uses the handle's scratch)
   if (d == 3 && mg.L > 1) {
     const size_t n3 = (size_t)(mg.Nl[1] / 3) * B;
@@ -554,9 +670,7 @@ cd_status mg_set_params_slots(MgData& mg, int d, int P, const std::vector<double
     if (nc >= 128) {
       CD_CUDA_OK(cudaMemcpyAsync(dst64, D.data(), D.size() * 8, cudaMemcpyHostToDevice, s));
       CD_CUDA_OK(cudaMemsetAsync(mg.tmpB, 0, sizeof(double), s));
-      spd_invert_kernel<<<1, 512, nc * sizeof(double), s>>>(nc, dst64, dst32,
-                                                            reinterpret_cast<int*>(mg.tmpB));
-      count_launch();
+      gpu_spd_invert(nc, 1, dst64, dst32, reinterpret_cast<int*>(mg.tmpB), mg.gjws, s);
       int bad = 0;
       CD_CUDA_OK(cudaMemcpyAsync(&bad, mg.tmpB, sizeof(int), cudaMemcpyDeviceToHost, s));
       CD_CUDA_OK(cudaStreamSynchronize(s));  // D goes out of scope
@@ -598,9 +712,7 @@ cd_status mg_set_params(MgData& mg, int d, int P, int nrhs, const std::vector<do
     }
     CD_CUDA_OK(cudaMemcpyAsync(mg.cinv64, inv64.data(), inv64.size() * 8, cudaMemcpyHostToDevice, s));
     CD_CUDA_OK(cudaMemsetAsync(mg.tmpB, 0, sizeof(double), s));
-    spd_invert_kernel<<<nrhs, 512, nc * sizeof(double), s>>>(nc, mg.cinv64, mg.cinv32,
-                                                             reinterpret_cast<int*>(mg.tmpB));
-    count_launch();
+    gpu_spd_invert(nc, nrhs, mg.cinv64, mg.cinv32, reinterpret_cast<int*>(mg.tmpB), mg.gjws, s);
     int bad = 0;
     CD_CUDA_OK(cudaMemcpyAsync(&bad, mg.tmpB, sizeof(int), cudaMemcpyDeviceToHost, s));
     CD_CUDA_OK(cudaStreamSynchronize(s));  // inv64 (host) goes out of scope

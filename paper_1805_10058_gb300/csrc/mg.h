@@ -37,6 +37,7 @@ struct MgData {
   void* scratch32 = nullptr;
   double* part = nullptr;     // partial sums [B][1024]
   double* tmpB = nullptr;     // [B]
+  double* gjws = nullptr;     // side buffer of the coarsest inversion (nc >= 128)
   double alpha_cache_ok = 0;
   // Krylov post-smoother of the finest level (Section 6.1), set up by mg_setup_ksmooth:
   // ks_steps iterations; vectors (2 ks_steps + 2 of [B][N_0] per precision), per-solve scalars

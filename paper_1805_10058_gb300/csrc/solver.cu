@@ -562,11 +562,11 @@ static cd_status solve_device(cd_solver h, const double* b, double* x, double* x
   count_launch(4);
   vzero<double>(N, B, x, nullptr, h->s);
   const bool ext = h->opt.ext_residual != 0;
-  // 2D mixed precision: the FP64 inner solves apply the operator in double-FP32 on the FP32
-  // pipe (the double-FP64 outer residual corrects its coarser rounding).  CD_PREC_FP64 keeps
-  // FP64 arithmetic throughout.
-  const bool emu_inner = ext && h->opt.emulated_fp64 && h->d == 2 &&
-                         h->opt.precision != CD_PREC_FP64;
+  // Mixed precision: the FP64 inner solves apply the operator in double-FP32 on the FP32 pipe
+  // (2D: the packed folded kernel; 3D: the tuned passes with (hi, lo) intermediates), and the
+  // double-FP64 outer residual corrects its coarser rounding.  CD_PREC_FP64 keeps FP64
+  // arithmetic throughout.
+  const bool emu_inner = ext && h->opt.emulated_fp64 && h->opt.precision != CD_PREC_FP64;
   double* xlo = ext ? h->xlo64.as<double>() : nullptr;
   if (ext) vzero<double>(N, B, xlo, nullptr, h->s);
   launch_dot<double>(b, b, N, B, h->part[1].as<double>(), nb, nullptr, h->s);
@@ -856,7 +856,7 @@ cd_status sess_step(cd_solver h, std::vector<int>& finished) {
   const long long N = h->N;
   const int pc = h->opt.precond;
   const bool ext = h->opt.ext_residual != 0;
-  const bool emu = ext && h->opt.emulated_fp64 && h->d == 2 && h->opt.precision != CD_PREC_FP64;
+  const bool emu = ext && h->opt.emulated_fp64 && h->opt.precision != CD_PREC_FP64;
   double* b = h->s_b.as<double>();
   double* x = h->s_x.as<double>();
   double* xlo = ext ? h->xlo64.as<double>() : nullptr;
@@ -1282,6 +1282,8 @@ cd_status cd_create(cd_solver* out, int d, int p, int n, double alpha, double be
     const std::string v3ds = v3d ? v3d : "";
     set_apply3d_variant(v3ds == "multipass" ? 0 : v3ds == "axis" ? 2 : v3ds == "stream" ? 3
                         : v3ds == "pass64" ? 4 : 1);
+    const char* vr = std::getenv("CURLDIV_FF2_ROWS");
+    set_ff2_rows(vr ? std::atoi(vr) : 0);
   }
   if (h->opt.precond == CD_PC_FD_D || h->opt.precond == CD_PC_FD_T) {
     cd_status st = ensure_fd(h.get());

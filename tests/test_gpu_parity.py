@@ -339,11 +339,12 @@ def test_host_entry_point_and_error_statuses():
         s.cd_apply(dev(np.zeros(3 * s.N)), dev(np.zeros(3 * s.N)))
 
 
-@pytest.mark.parametrize("p,n,beta", [(2, 16, 0.3), (3, 13, 50.0)])
+@pytest.mark.parametrize("p,n,beta", [(2, 16, 0.3), (3, 13, 50.0), (5, 12, 1e3), (4, 9, 1e-2)])
 def test_mg_single_level_is_the_dense_inverse(p, n, beta):
     """2D multigrid on a mesh at or below its coarsest size (m <= 16): the V-cycle is the dense
     coarse solve alone, whose SPD inverse (2 m^2 >= 128 unknowns) is formed on the GPU by
-    Gauss-Jordan elimination, so cd_precond(MG) r = A^{-1} r up to the conditioning."""
+    blocked Gauss-Jordan elimination (orders 242-512, full and ragged panels and tiles), so
+    cd_precond(MG) r = A^{-1} r up to the conditioning."""
     s = cdl.Solver(2, p, n, max_batch=2, precond=cdl.CD_PC_MG)
     assert s.cd_levels() == 1
     R = inputs.uniform_rhs(2, p, n, seed=9, nrhs=2)
