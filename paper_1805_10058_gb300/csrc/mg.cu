@@ -22,7 +22,24 @@ MgData::~MgData() {
 // The tap weights (1, 1/2, 1/4, 1/8) are exact in every precision; the index arithmetic is 32-bit
 // (one solve's vector has fewer than 2^31 entries on every level this library builds: the
 // set-up rejects larger problems).
-template <typename T>
+// Accumulation type A: T itself, or float for FP64 vectors whose transfers run on the FP32 pipe
+// (the FP64 inner solves with double-FP32 applies): the taps' FP32 truncations (integer
+// operations) are summed in FP32 and the sum is widened exactly, leaving one FP64 operation per
+// output (the prolongation's add) instead of several on GB300's narrow FP64 pipe.  A multigrid
+// correction, like a smoother step, needs no more than FP32 accuracy inside a flexible Krylov
+// solve whose residuals stay FP64.
+template <typename A, typename T>
+__device__ __forceinline__ A tap_load(T v) {
+  if constexpr (sizeof(A) == 4 && sizeof(T) == 8) return ff_split_bits(v).x;
+  else return (A)v;
+}
+template <typename T, typename A>
+__device__ __forceinline__ T tap_widen(A v) {
+  if constexpr (sizeof(A) == 4 && sizeof(T) == 8) return f2d_bits(v);
+  else return (T)v;
+}
+
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) restrict_kernel(int d, int mf, int mc, const T* __restrict__ fine,
                                                        T* __restrict__ coarse,
                                                        const int* __restrict__ active) {
@@ -42,50 +59,50 @@ __global__ void __launch_bounds__(256) restrict_kernel(int d, int mf, int mc, co
       rem = q;
     }
     const T* src = fb + (long long)comp * nfc;
-    T acc = 0;
+    A acc = 0;
     if (d == 2) {
 #pragma unroll
       for (int a0 = 0; a0 < 3; ++a0) {
         const int i0 = 2 * J[0] + a0;
         if (i0 >= mf) break;
-        T row = 0;
+        A row = 0;
 #pragma unroll
         for (int a1 = 0; a1 < 3; ++a1) {
           const int i1 = 2 * J[1] + a1;
           if (i1 >= mf) break;
-          const T v = src[i0 * mf + i1];
-          row += a1 == 1 ? v : T(0.5) * v;
+          const A v = tap_load<A>(src[i0 * mf + i1]);
+          row += a1 == 1 ? v : A(0.5) * v;
         }
-        acc += a0 == 1 ? row : T(0.5) * row;
+        acc += a0 == 1 ? row : A(0.5) * row;
       }
     } else {
 #pragma unroll 1
       for (int a0 = 0; a0 < 3; ++a0) {
         const int i0 = 2 * J[0] + a0;
         if (i0 >= mf) break;
-        T pl = 0;
+        A pl = 0;
         for (int a1 = 0; a1 < 3; ++a1) {
           const int i1 = 2 * J[1] + a1;
           if (i1 >= mf) break;
-          T row = 0;
+          A row = 0;
 #pragma unroll
           for (int a2 = 0; a2 < 3; ++a2) {
             const int i2 = 2 * J[2] + a2;
             if (i2 >= mf) break;
-            const T v = src[((long long)i0 * mf + i1) * mf + i2];
-            row += a2 == 1 ? v : T(0.5) * v;
+            const A v = tap_load<A>(src[((long long)i0 * mf + i1) * mf + i2]);
+            row += a2 == 1 ? v : A(0.5) * v;
           }
-          pl += a1 == 1 ? row : T(0.5) * row;
+          pl += a1 == 1 ? row : A(0.5) * row;
         }
-        acc += a0 == 1 ? pl : T(0.5) * pl;
+        acc += a0 == 1 ? pl : A(0.5) * pl;
       }
     }
-    cb[idx] = acc;
+    cb[idx] = tap_widen<T>(acc);
   }
 }
 
 // fine(i) += sum_J prod_l P(i_l, J_l) coarse(J); P(i, J) = 1 if i = 2J+1, 1/2 if i = 2J or 2J+2
-template <typename T>
+template <typename T, typename A>
 __global__ void __launch_bounds__(256) prolong_kernel(int d, int mf, int mc, const T* __restrict__ coarse,
                                                       T* __restrict__ fine,
                                                       const int* __restrict__ active) {
@@ -120,44 +137,44 @@ __global__ void __launch_bounds__(256) prolong_kernel(int d, int mf, int mc, con
       }
     }
     const T* src = cb + (long long)comp * ncc;
-    T acc = 0;
+    A acc = 0;
     if (d == 2) {
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const int ja = a == 0 ? j0[0] : j1[0];
         if (ja < 0 || ja >= mc) continue;
-        T row = 0;
+        A row = 0;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           const int jc = c == 0 ? j0[1] : j1[1];
           if (jc < 0 || jc >= mc) continue;
-          row += src[ja * mc + jc];
+          row += tap_load<A>(src[ja * mc + jc]);
         }
-        acc += half[1] ? T(0.5) * row : row;
+        acc += half[1] ? A(0.5) * row : row;
       }
-      if (half[0]) acc = T(0.5) * acc;
+      if (half[0]) acc = A(0.5) * acc;
     } else {
       for (int a = 0; a < 2; ++a) {
         const int ja = a == 0 ? j0[0] : j1[0];
         if (ja < 0 || ja >= mc) continue;
-        T pl = 0;
+        A pl = 0;
         for (int c = 0; c < 2; ++c) {
           const int jc = c == 0 ? j0[1] : j1[1];
           if (jc < 0 || jc >= mc) continue;
-          T row = 0;
+          A row = 0;
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const int je = e == 0 ? j0[2] : j1[2];
             if (je < 0 || je >= mc) continue;
-            row += src[((long long)ja * mc + jc) * mc + je];
+            row += tap_load<A>(src[((long long)ja * mc + jc) * mc + je]);
           }
-          pl += half[2] ? T(0.5) * row : row;
+          pl += half[2] ? A(0.5) * row : row;
         }
-        acc += half[1] ? T(0.5) * pl : pl;
+        acc += half[1] ? A(0.5) * pl : pl;
       }
-      if (half[0]) acc = T(0.5) * acc;
+      if (half[0]) acc = A(0.5) * acc;
     }
-    fb[idx] += acc;
+    fb[idx] += tap_widen<T>(acc);
   }
 }
 
@@ -172,7 +189,10 @@ void mg_restrict(int d, int mf, int mc, int B, const T* fine, T* coarse, const i
                  cudaStream_t s) {
   long long nc = d;
   for (int l = 0; l < d; ++l) nc *= mc;
-  restrict_kernel<T><<<grid_for(nc, B), 256, 0, s>>>(d, mf, mc, fine, coarse, active);
+  if (sizeof(T) == 8 && fp64_emulated())
+    restrict_kernel<T, float><<<grid_for(nc, B), 256, 0, s>>>(d, mf, mc, fine, coarse, active);
+  else
+    restrict_kernel<T, T><<<grid_for(nc, B), 256, 0, s>>>(d, mf, mc, fine, coarse, active);
   count_launch();
 }
 template <typename T>
@@ -180,7 +200,10 @@ void mg_prolong_add(int d, int mf, int mc, int B, const T* coarse, T* fine, cons
                     cudaStream_t s) {
   long long nf = d;
   for (int l = 0; l < d; ++l) nf *= mf;
-  prolong_kernel<T><<<grid_for(nf, B), 256, 0, s>>>(d, mf, mc, coarse, fine, active);
+  if (sizeof(T) == 8 && fp64_emulated())
+    prolong_kernel<T, float><<<grid_for(nf, B), 256, 0, s>>>(d, mf, mc, coarse, fine, active);
+  else
+    prolong_kernel<T, T><<<grid_for(nf, B), 256, 0, s>>>(d, mf, mc, coarse, fine, active);
   count_launch();
 }
 template void mg_restrict<double>(int, int, int, int, const double*, double*, const int*, cudaStream_t);
