@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "apply_shared.h"
 #include "ffmath.h"
@@ -571,7 +572,7 @@ static bool stencil_ff2(const StencilHost& sh, StencilFF2& cs) {
 
 // Tile rows of the double-FP32 2D apply: 0 = chosen by the grid size, else kNarrowRows or the wide
 // tile (any other value).
-static int g_ff2_rows = 0;
+static std::atomic<int> g_ff2_rows{0};  // set at every handle creation, from any thread
 static constexpr int kNarrowRows = 8;
 void set_ff2_rows(int rows) { g_ff2_rows = rows; }
 

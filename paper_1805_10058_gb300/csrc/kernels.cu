@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -28,7 +29,7 @@
 
 namespace cd {
 
-static int g_use_stream3d = 1;  // 3D: 1 = streaming fused kernel, 0 = three banded passes
+static std::atomic<int> g_use_stream3d{1};  // 3D: 1 = streaming fused kernel, 0 = three banded passes
 
 // ------------------------------------------------------------------ helpers
 
@@ -1668,22 +1669,21 @@ static int tuned_variant(size_t es, int m, int P, int /*B*/) {
   return it == g_tuned.end() ? 0 : it->second;
 }
 int num_sms() {
-  static int n = 0;
-  if (n == 0) {
+  static const int n = [] {
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-      n = v;
-    else
-      return 148;
-  }
+      return v;
+    cudaGetLastError();
+    return 148;
+  }();
   return n;
 }
-static int g_use_v2 = 2;  // 2: v5 then v3 kernel (FP32), 3: v3 only, 1: v2 kernel, 0: v1 kernel
+static std::atomic<int> g_use_v2{2};  // 2: v5 then v3 kernel (FP32), 3: v3 only, 1: v2 kernel, 0: v1 kernel
 void set_apply_variant(int v) { g_use_v2 = v; }
-static int g_fp64_v3 = 0;    // FP64 2D apply: 0 = v2 (default), 1 = v3 (8 rows per tile)
-static int g_ff_forced = 0;  // 1: every FP64 2D apply in double-FP32 (kernel checks)
-static int g_ff_kernel = 2;  // double-FP32 2D apply: 2 = packed folded kernel, 1 = plain kernel
+static std::atomic<int> g_fp64_v3{0};    // FP64 2D apply: 0 = v2 (default), 1 = v3 (8 rows per tile)
+static std::atomic<int> g_ff_forced{0};  // 1: every FP64 2D apply in double-FP32 (kernel checks)
+static std::atomic<int> g_ff_kernel{2};  // double-FP32 2D apply: 2 = packed folded kernel, 1 = plain kernel
 void set_apply_fp64_variant(int v) {
   g_fp64_v3 = v == 1;
   g_ff_forced = v == 2 || v == 3 || v == 4;
@@ -1692,8 +1692,8 @@ void set_apply_fp64_variant(int v) {
 // 3D designs.  g_use_pass3d: 1 = tuned pass kernels (FP64: generic axis passes), 2 = tuned pass
 // kernels in FP64 too, 0 = generic axis passes only.  g_stream_forced: the streaming kernel
 // whenever it applies (FP32, P <= 4).
-static int g_use_pass3d = 1;
-static int g_stream_forced = 0;
+static std::atomic<int> g_use_pass3d{1};
+static std::atomic<int> g_stream_forced{0};
 // 0: passes, 1: automatic (the autotuner may choose the streaming kernel), 2: generic axis
 // passes, 3: streaming kernel forced, 4: tuned passes in FP64 as well
 void set_apply3d_variant(int v) {
