@@ -1,6 +1,6 @@
 // The 2D operator apply in double-FP32 arithmetic: FP64 vectors, every product and sum of the
-// sum-factorised stencil (Section 2's Kronecker form of the 2D block operator) carried as an
-// unevaluated sum of two FP32 numbers on the FP32 pipe.
+// sum-factorised stencil (the Kronecker form of the 2D block matrix, Section 4.1, eq:matr_Amu)
+// carried as an unevaluated sum of two FP32 numbers on the FP32 pipe.
 #include <cuda_runtime.h>
 
 #include <algorithm>

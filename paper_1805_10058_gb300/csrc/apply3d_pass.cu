@@ -1,5 +1,5 @@
 // The 3D operator apply as three tuned banded passes (sum factorisation of the Kronecker form
-// of the 3D block operator, Section 2), in FP32, FP64 or double-FP32.
+// of the 3D block matrix, Section 4.2, eq:matr_Amu3D), in FP32, FP64 or double-FP32.
 #include <cuda_runtime.h>
 
 #include <algorithm>
