@@ -196,7 +196,9 @@ static bool launch_ff_P(int m, const double* bands, const StencilHost& sh, const
 //  * shared memory rows have an odd number of 16-byte slots, so the column-wise x_2 pass (lanes
 //    = rows) and the row-wise x_1 pass (lanes = columns) are both free of bank conflicts.
 // Tile: TR = 24 (P <= 4) or 20 output rows x 32 columns per CTA of 128 threads; the x_2 pass
-// covers the TR + 2P <= 32 rows of the halo, one row per lane.
+// covers the TR + 2P <= 32 rows of the halo, one row per lane.  The narrow variant (TR = 8, for
+// grids too small to fill the GPU with wide tiles) hands the x_2 pass's (halo row, column group)
+// pairs to all 128 threads, so a CTA's serial chain is about a third as long.
 struct FF2 {  // two double-FP32 numbers: (h.x + l.x, h.y + l.y)
   float2 h, l;
 };
